@@ -1,0 +1,359 @@
+#!/usr/bin/env python3
+"""Benchmark of SIVF spherical k-means on GB300.
+
+Workload (default): the medium single-GPU corpus, N = 300,000 documents,
+D = 100,000 terms, Zipf s = 1.05, lognormal(5.0, 0.7) lengths clipped to
+[10, 3000] (~190 nnz/doc, 57M nnz), k = 1000, FP32 postings, ICP on.
+
+A step is one complete clustering run from the seeded initial centroids:
+seeding + up to 50 Lloyd iterations (assignment, Algorithm 4, and update,
+Algorithm 5), every step identical. `value` = objects assigned per second
+(N * iterations / step time), inputs resident in HBM; `e2e` = the same metric
+through the C ABI with the corpus in pinned host memory and the labels copied
+back, every step.
+
+--impl reference times the FP64 CPU oracle (the plain restatement of the
+method) on the host cores instead: each step is one Lloyd iteration of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from synth import CONFIGS, generate, init_ids  # noqa: E402
+
+B_POST = {"fp32": 8, "bf16": 6, "fp16": 6}  # bytes per posting (int32 id + value)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--icp", type=int, default=1)
+    ap.add_argument("--max-iter", type=int, default=None)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-iters", type=int, default=8)
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier_and_sync(world):
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_baseline(w, c, ini, iters):
+    """The FP64 oracle (OpenMP, all host cores) on a bounded sample of the same
+    workload: the first `iters` Lloyd iterations (assign + update)."""
+    from oracle import Oracle
+    o = Oracle(c, w.k, ini, icp=True)
+    t0 = time.perf_counter()
+    done = 0
+    for _ in range(iters):
+        a = o.assign()
+        done += 1
+        if a.r > 1 and a.changed == 0:
+            break
+        o.update()
+    dt = time.perf_counter() - t0
+    return {"value": w.N * done / dt, "unit": "objects/s", "cores": Oracle.threads(), "kind": "oracle",
+            "sample": f"first {done} Lloyd iterations (assign+update) of the same corpus, FP64 oracle, "
+                      f"{dt:.1f} s", "sec_per_iter": dt / done}
+
+
+def run_reference(args, w):
+    """Reference arm: the FP64 CPU oracle, each step one Lloyd iteration."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    from oracle import Oracle
+    c = generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, w.seed)
+    ini = init_ids(w.N, w.k, w.init_seed)
+    o = Oracle(c, w.k, ini, icp=bool(args.icp))
+
+    def step():
+        a = o.assign()
+        if a.r > 1 and a.changed == 0:
+            o.set_labels(o.labels())
+        o.update()
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = w.N * args.steps / dt
+    line = {"metric": "objects/s (Lloyd iterations of SIVF spherical k-means)", "value": value, "unit": "objects/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"{w.name}: N={w.N} D={w.D} k={w.k} zipf={w.zipf_s}", "iters_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": "objects/s", "cores": Oracle.threads(), "kind": "oracle",
+                             "sample": f"iterations {args.warmup + 1}..{args.warmup + args.steps} of the corpus"},
+            "e2e": {"value": value, "unit": "objects/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    w = CONFIGS[args.config]
+    if args.precision:
+        w = w.scaled(precision=args.precision)
+    if args.max_iter:
+        w = w.scaled(max_iter=args.max_iter)
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    from paper_2103_16141_gb300 import SIVF, sivf as S
+
+    world, rank, local = dist_setup(args.gpus)
+    S.load()
+    # each rank is an independent replica of the workload (the path needs no exchange)
+    c = generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, w.seed)
+    ini = init_ids(w.N, w.k, w.init_seed)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = SIVF(c.row_ptr, c.idx, c.val, c.D, w.k, ini, precision=w.precision, icp=bool(args.icp),
+             threads=args.threads, ctas_per_sm=args.ctas_per_sm)
+    stream = torch.cuda.current_stream()
+
+    def one_run():
+        g.reseed(ini)
+        iters = 0
+        per = []
+        launches_at_seed = 0
+        for _ in range(w.max_iter):
+            n = g.assign()
+            iters += 1
+            st = g.stats()
+            per.append(st)
+            if st["iter"] > 1 and n == 0:
+                break
+            g.update()
+            per[-1] = {**st, "ms_update": g.stats()["ms_update"], "centroid_nnz": g.stats()["centroid_nnz"]}
+        per[-1]["launches_run"] = g.stats()["launches"] - launches_at_seed  # reseed resets the count
+        return iters, per
+
+    for _ in range(args.warmup):
+        one_run()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier_and_sync(world)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    tot_iters, all_per = 0, []
+    for _ in range(args.steps):
+        it, per = one_run()
+        tot_iters += it
+        all_per.extend(per)
+    ev1.record(stream)
+    barrier_and_sync(world)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ms, world)
+    launches = sum(p["launches_run"] for p in all_per if "launches_run" in p)
+    objects = sum_over_ranks(float(w.N * tot_iters), world)
+    value = objects / (ms / 1e3)
+
+    # roofline of the dominant kernel (the assignment scan), live from the
+    # library's per-launch event timings over the timed region
+    hbm_peak, peak_src = load_peaks()
+    b_post = B_POST[w.precision]
+    alg_bytes = sum(c.nnz * 8 + (w.N + 1) * 8 + p["postings"] * b_post + w.N * 16 + w.k for p in all_per)
+    ms_assign = sum(p["ms_assign"] for p in all_per)
+    ms_update = sum(p.get("ms_update", 0.0) for p in all_per)
+    achieved = alg_bytes / (ms_assign / 1e3) / 1e9 if ms_assign > 0 else 0.0
+    postings = sum(p["postings"] for p in all_per)
+    iters_per_step = tot_iters / args.steps
+
+    # end to end: host corpus in pinned memory -> device, init, run, labels back
+    e2e = None
+    if not args.no_e2e:
+        rp = torch.from_numpy(c.row_ptr).pin_memory()
+        ix = torch.from_numpy(c.idx).pin_memory()
+        vl = torch.from_numpy(c.val).pin_memory()
+        lab_host = torch.empty(w.N, dtype=torch.int32).pin_memory()
+        h2d = rp.numel() * 8 + ix.numel() * 4 + vl.numel() * 4
+        d2h = w.N * 4
+        barrier_and_sync(world)
+        t0 = time.perf_counter()
+        e_iters = 0
+        E = max(1, min(args.steps, 3))
+        for _ in range(E):
+            d_rp = rp.to(dev, non_blocking=True)
+            d_ix = ix.to(dev, non_blocking=True)
+            d_vl = vl.to(dev, non_blocking=True)
+            ge = SIVF(d_rp, d_ix, d_vl, c.D, w.k, ini, precision=w.precision, icp=bool(args.icp),
+                      threads=args.threads, ctas_per_sm=args.ctas_per_sm)
+            it, _ = ge.run(w.max_iter)
+            e_iters += it
+            S.sivf_get_labels(ge.ctx, lab_host.data_ptr(), False)
+            ge.close()
+        barrier_and_sync(world)
+        dt = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": sum_over_ranks(float(w.N * e_iters), world) / dt, "unit": "objects/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": E}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, c, ini, args.cpu_sample_iters)
+
+    if rank == 0:
+        line = {
+            "metric": "objects/s (Lloyd iterations of SIVF spherical k-means); sec per Lloyd iteration",
+            "value": value, "unit": "objects/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if w.precision == "fp32" else f"{w.precision}-postings/f32-products/fixed-point-sum",
+            "data": "synthetic",
+            "config": {"workload": f"{w.name}: N={w.N} D={w.D} nnz={c.nnz} k={w.k} zipf={w.zipf_s} "
+                                   f"len=lognormal({w.mu:.3f},{w.sigma}) clip[{w.lo},{w.hi}] seed={w.seed}",
+                       "precision": w.precision, "icp": bool(args.icp), "max_iter": w.max_iter,
+                       "iters_per_step": iters_per_step, "sec_per_iter": ms / 1e3 / tot_iters,
+                       "l2": "inputs larger than L2 (CSR 0.46 GB; inverted file > 129 MB)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                         "kernel": "assign_kernel", "bytes_model": "nnz*8 + (N+1)*8 + postings*b_post + N*16 + k",
+                         "postings_per_s": postings / (ms_assign / 1e3) if ms_assign > 0 else None,
+                         "ms_assign_per_iter": ms_assign / tot_iters, "ms_update_per_iter": ms_update / tot_iters},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        if e2e:
+            line["e2e"] = e2e
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

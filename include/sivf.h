@@ -1,0 +1,191 @@
+/*
+ * sivf.h — C ABI of the GB300 (sm_103a) implementation of SIVF spherical
+ * k-means: the structured inverted-file assignment step with the invariant
+ * centroid-pair (ICP) filter, and the update step that rebuilds the file.
+ *
+ * Method: Aoyama & Saito, "Structured Inverted-File k-Means Clustering for
+ * High-Dimensional Sparse Data", arXiv 2103.16141.
+ *   - problem and objective: Section 1 (spherical k-means: unit-length
+ *     objects and means, cosine similarity), Section 2.1 Eq. (1) and
+ *     Algorithm 1 (Lloyd iteration);
+ *   - assignment step: Algorithm 4 (Section 4.1), with the unfiltered
+ *     inverted-file assignment of Algorithm 2 (Section 3.2) as the icp = 0 mode;
+ *   - update step and structured inverted file: Algorithm 5 (Section 4.2).
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns a sivf_status and never aborts or traps.
+ *   - An invalid argument returns SIVF_ERR_INVALID_ARG (or SIVF_ERR_BAD_CSR)
+ *     and leaves the context unchanged.
+ *   - A CUDA failure returns SIVF_ERR_CUDA; after it the context is latched:
+ *     every later call except the getters of sivf_last_error and
+ *     sivf_destroy returns SIVF_ERR_STATE.
+ *   - All device work is ordered on the stream passed to sivf_init. Calls
+ *     that return host values synchronise that stream.
+ *   - Labels are 0-based cluster ids in [0, k).
+ *   - "DEVICE" pointers are CUDA device (or managed) memory; "HOST" pointers
+ *     are ordinary host memory.
+ */
+#ifndef SIVF_H
+#define SIVF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SIVF_OK = 0,
+    SIVF_ERR_INVALID_ARG = 1,
+    SIVF_ERR_BAD_CSR = 2,
+    SIVF_ERR_OOM = 3,
+    SIVF_ERR_CUDA = 4,
+    SIVF_ERR_TIMEOUT = 5,
+    SIVF_ERR_STATE = 6
+} sivf_status;
+
+/* Storage precision of the inverted-file posting values used by the
+ * assignment scan. Products are formed in FP32 and accumulated exactly in
+ * fixed point; objects whose top-2 margin is inside the derived error bound
+ * are re-scored in FP64 from the FP32 centroid values, so the labels do not
+ * depend on this choice. */
+typedef enum { SIVF_FP32 = 0, SIVF_BF16 = 1, SIVF_FP16 = 2 } sivf_precision;
+
+typedef struct {
+    sivf_precision prec; /* posting value precision for the scan */
+    int icp;             /* 1: ICP filter (Algorithm 4); 0: unfiltered (Algorithm 2) */
+    int threads;         /* threads per CTA of the assignment kernel; 0 = automatic */
+    int ctas_per_sm;     /* resident CTAs per SM of the assignment kernel; 0 = automatic */
+    int64_t mem_cap_bytes; /* cap on library-owned device memory; 0 = no cap */
+} sivf_config;
+
+/* Counters of the most recent assignment / update (host copy). */
+typedef struct {
+    int32_t iter;            /* r: number of assignment steps done */
+    int64_t changed;         /* objects whose label changed at r (N at r = 1) */
+    int64_t n_moving;        /* clusters with lambda^[r] = 0 */
+    int64_t n_moving_prev;   /* clusters with lambda^[r-1] = 0 (candidates of a filtered object) */
+    int64_t filtered;        /* objects that took the filtered (front-only) branch */
+    int64_t simcalc;         /* similarity calculations: k per unfiltered, n_moving_prev per filtered object */
+    int64_t postings;        /* postings visited by the scan */
+    int64_t rescored;        /* objects re-scored in FP64 (top-2 margin inside the error bound) */
+    int64_t rescore_cands;   /* candidate centroids re-scored in FP64 */
+    int64_t centroid_nnz;    /* non-zeros of the centroid set M^[r] after the last update */
+    int64_t moved_nnz;       /* object non-zeros gathered by the last update (members of moving clusters) */
+    double objective_assign; /* J^[r] = sum_i <x_i, mu_{a(i)}^[r-1]> (FP64) */
+    double objective_update; /* sum_j ||s_j^[r]||, s_j = sum of members (FP64) */
+    double ms_assign;        /* device time of the last assignment step */
+    double ms_update;        /* device time of the last update step */
+    int64_t launches;        /* kernels launched by the library since sivf_init / sivf_reseed */
+} sivf_stats;
+
+typedef struct sivf_ctx sivf_ctx; /* opaque, library-owned */
+
+/*
+ * sivf_init — validate the object set, copy the initial centroids and build
+ * the first inverted file (Algorithm 1 input M^[0]; Algorithm 5 layout with
+ * every centroid moving, since lambda^[0] = 0).
+ *   out      : HOST, receives the new context (NULL on failure).
+ *   cfg      : HOST, copied; NULL means defaults (FP32, icp = 1).
+ *   N, D, k  : objects, vocabulary size, clusters; 1 <= k <= N, D >= 1.
+ *   row_ptr  : DEVICE int64[N+1], CSR row offsets, row_ptr[0] = 0, non-decreasing.
+ *   idx      : DEVICE int32[nnz], term ids in [0, D), strictly ascending in each row.
+ *   val      : DEVICE float[nnz], tf-idf values > 0, each row of unit L2 norm.
+ *              row_ptr / idx / val are BORROWED: they must stay valid and
+ *              unchanged until sivf_destroy.
+ *   init_ids : HOST int32[k], distinct object ids; mu_j^[0] = x_{init_ids[j]}. Copied.
+ *   stream   : cudaStream_t (may be NULL = legacy default stream).
+ * Errors: SIVF_ERR_INVALID_ARG (sizes, ids), SIVF_ERR_BAD_CSR (row_ptr not
+ * monotone, idx out of range or not ascending, val not finite and positive,
+ * a row norm off 1 by more than 1e-4), SIVF_ERR_OOM, SIVF_ERR_CUDA.
+ */
+sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t D, int32_t k,
+                      const int64_t *row_ptr, const int32_t *idx, const float *val,
+                      const int32_t *init_ids, void *stream);
+
+/*
+ * sivf_reseed — restart the context from new initial centroids without
+ * reallocating: mu_j^[0] = x_{init_ids[j]}, no labels, every cluster moving,
+ * first inverted file rebuilt (same as the tail of sivf_init).
+ *   init_ids : HOST int32[k], distinct object ids. Copied.
+ * Errors: SIVF_ERR_INVALID_ARG (ids), SIVF_ERR_CUDA.
+ */
+sivf_status sivf_reseed(sivf_ctx *ctx, const int32_t *init_ids);
+
+/*
+ * sivf_assign — one assignment step (Algorithm 4; Algorithm 2 when icp = 0):
+ * scores every object against the structured inverted file, takes the argmax
+ * (largest score, lowest index on ties), and marks invariant clusters
+ * (lambda_j^[r] = 1 iff no object entered or left cluster j).
+ *   n_changed : HOST out, may be NULL; objects whose label changed.
+ * Synchronises the stream. Two assignments must be separated by an update
+ * (the inverted file is laid out for the lambda of the previous step):
+ * otherwise SIVF_ERR_STATE, context unchanged.
+ */
+sivf_status sivf_assign(sivf_ctx *ctx, int64_t *n_changed);
+
+/*
+ * sivf_update — one update step (Algorithm 5): means of the moving clusters,
+ * normalised to unit length in FP64 and stored as FP32; invariant and empty
+ * clusters keep their centroid; the structured inverted file is rebuilt
+ * (moving centroids in front, invariant behind, ascending ids in each part).
+ * Requires at least one assignment (or sivf_set_labels) since sivf_init.
+ */
+sivf_status sivf_update(sivf_ctx *ctx);
+
+/*
+ * sivf_run — Algorithm 1 loop: assign, then update, until an assignment
+ * (r > 1) changes no label or max_iter assignments have run.
+ *   iters_out     : HOST out, may be NULL; assignment steps run by this call.
+ *   objective_out : HOST out, may be NULL; J of the last assignment.
+ */
+sivf_status sivf_run(sivf_ctx *ctx, int32_t max_iter, int32_t *iters_out, double *objective_out);
+
+/* sivf_get_labels — copy N labels to dst (DEVICE if dst_is_device, else HOST). */
+sivf_status sivf_get_labels(sivf_ctx *ctx, int32_t *dst, int dst_is_device);
+
+/*
+ * sivf_set_labels — replace the labels (resume from a checkpoint, or lockstep
+ * resynchronisation). src: N labels in [0, k) (DEVICE if src_is_device).
+ * Clusters whose membership changes become moving; objects whose label
+ * changes lose their stored own-cluster score and take the unfiltered branch
+ * at the next assignment. Call sivf_update afterwards to rebuild the means.
+ */
+sivf_status sivf_set_labels(sivf_ctx *ctx, const int32_t *src, int src_is_device);
+
+/*
+ * sivf_get_centroids — cluster-major FP32 centroids (the master copy):
+ *   off  : HOST int64[k+1] (always written),
+ *   term : HOST int32[cap], u : HOST float[cap] (written if cap >= nnz),
+ *   nnz_out : HOST, receives the centroid non-zero count.
+ * Returns SIVF_ERR_INVALID_ARG (after writing off and nnz_out) if cap < nnz.
+ */
+sivf_status sivf_get_centroids(sivf_ctx *ctx, int64_t *off, int32_t *term, float *u, int64_t cap,
+                               int64_t *nnz_out);
+
+/*
+ * sivf_get_inverted_file — the structured inverted file (Algorithm 5 output):
+ *   off : HOST int64[D+1], mf0 : HOST int32[D] (front length),
+ *   cid : HOST int32[cap], u : HOST float[cap] (FP32 values), nnz_out.
+ * Same capacity rule as sivf_get_centroids.
+ */
+sivf_status sivf_get_inverted_file(sivf_ctx *ctx, int64_t *off, int32_t *mf0, int32_t *cid, float *u,
+                                   int64_t cap, int64_t *nnz_out);
+
+/* sivf_get_lambda — copy lambda^[r] (k bytes, 1 = invariant) to HOST dst. */
+sivf_status sivf_get_lambda(sivf_ctx *ctx, uint8_t *dst);
+
+/* sivf_get_stats — counters of the last assignment and update (HOST out). */
+sivf_status sivf_get_stats(sivf_ctx *ctx, sivf_stats *out);
+
+/* sivf_last_error — context-owned message of the last failure ("" if none);
+ * valid until the next call on ctx. Accepts NULL (returns a static string). */
+const char *sivf_last_error(const sivf_ctx *ctx);
+
+/* sivf_destroy — free all library-owned device memory. Accepts NULL. */
+void sivf_destroy(sivf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIVF_H */

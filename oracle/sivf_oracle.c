@@ -405,24 +405,30 @@ int orc_update(orc *o, double *stats) {
     return 0;
 }
 
-/* Replace the current labels (resume / lockstep resynchronisation). Clusters
- * whose membership changes become moving; objects whose label changes lose
- * their stored own score and take the unfiltered branch next time. */
+/* Replace a^[r] (resume / lockstep resynchronisation). lambda^[r] is
+ * recomputed against a^[r-1] (every cluster moving before the second
+ * assignment); objects whose label changes lose their stored own score and
+ * take the unfiltered branch next time. */
 int orc_set_labels(orc *o, const int32_t *labels) {
     for (int64_t i = 0; i < o->N; ++i)
         if (labels[i] < 0 || labels[i] >= o->k) return -1;
-    if (o->iter == 0) {
+    for (int64_t i = 0; i < o->N; ++i) {
+        if (o->labels[i] != labels[i]) {
+            o->labels[i] = labels[i];
+            o->own_ok[i] = 0;
+        }
+    }
+    if (o->iter <= 1) {
         memset(o->lambda, 0, (size_t)o->k);
-        for (int64_t i = 0; i < o->N; ++i) { o->labels[i] = labels[i]; o->own_ok[i] = 0; }
         o->iter = 1;
         return 0;
     }
+    memset(o->lambda, 1, (size_t)o->k);
     for (int64_t i = 0; i < o->N; ++i) {
-        if (o->labels[i] != labels[i]) {
-            if (o->labels[i] >= 0) o->lambda[o->labels[i]] = 0;
-            o->lambda[labels[i]] = 0;
-            o->labels[i] = labels[i];
-            o->own_ok[i] = 0;
+        int32_t a0 = o->prev_labels[i], a1 = o->labels[i];
+        if (a0 != a1) {
+            if (a0 >= 0) o->lambda[a0] = 0;
+            o->lambda[a1] = 0;
         }
     }
     return 0;

@@ -1,0 +1,495 @@
+// Assignment step of SIVF (Algorithm 4, Section 4.1; Algorithm 2 when the
+// ICP filter is off) on sm_103a.
+//
+// One CTA scores one object at a time (persistent CTAs pull object ids from a
+// global counter). The k similarities rho_j live in shared memory as unsigned
+// fixed-point sums with quantum 2^-31: each posting adds
+// q = ceil(fl(v * u) * 2^31) with an integer shared-memory atomic. Integer
+// addition is associative, so the sums do not depend on the order in which
+// threads visit postings: the filtered and unfiltered modes produce identical
+// scores, and every run is deterministic.
+//
+// ICP gate (Algorithm 4, line 6): if lambda^[r-1] of the object's cluster is 1,
+// only the front part [off_s, off_s + mf0_s) of each posting list is scanned,
+// and the candidates are the moving centroids plus the object's own cluster,
+// whose score is carried from its previous scan (it is unchanged because that
+// centroid is invariant).
+//
+// Argmax (Algorithm 4, lines 14-16): largest score, lowest index on ties.
+// Every object whose top-2 margin lies inside the rigorous error bound E of
+// the fixed-point / reduced-precision score is re-scored exactly: each
+// candidate within 2E of the best gets an FP64 dot product against its FP32
+// master centroid row, so the label equals the argmax of the exact scores
+// whatever the posting precision.
+//
+// Error bound (all terms v > 0, u > 0; master value u, stored value u~ with
+// |u~ - u| <= eps*u + eta; n terms in the object, S = sum of its values):
+//   |rho~ - rho| <= c*rho + a,  c = 2^-24 (1 + eps) + eps,
+//                               a = n * 2^-31 + (1 + 2^-24) * eta * S
+//   =>  E(rho~) = (c * rho~ + a) / (1 - c).
+// The 2^-24 term is the FP32 rounding of the product, n * 2^-31 the one-sided
+// fixed-point rounding of the n products.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "sivf_internal.cuh"
+
+namespace sivf {
+namespace {
+
+struct AssignParams {
+    int64_t N;
+    int32_t k;
+    int icp;
+    const int64_t *row_ptr;
+    const int32_t *idx;
+    const float *val;
+    const float *sumv;
+    const int64_t *if_off;
+    const int32_t *if_mf0;
+    const int32_t *if_cid;
+    const void *if_vals;
+    const int64_t *coff;
+    const int32_t *cterm;
+    const float *cval;
+    const int32_t *labels_prev;
+    int32_t *labels;
+    uint32_t *own;
+    const uint8_t *lam_prev;
+    const int32_t *mov_list;
+    const int32_t *n_mov;
+    uint8_t *moving;
+    DevCounters *ctr;
+    double eps, eta;
+};
+
+template <int PREC>
+__device__ __forceinline__ float load_u(const void *p, int pos) {
+    if (PREC == SIVF_FP32) {
+        return __ldg(reinterpret_cast<const float *>(p) + pos);
+    } else if (PREC == SIVF_BF16) {
+        unsigned short b = __ldg(reinterpret_cast<const unsigned short *>(p) + pos);
+        return __uint_as_float(((unsigned)b) << 16);
+    } else {
+        unsigned short b = __ldg(reinterpret_cast<const unsigned short *>(p) + pos);
+        return __half2float(__ushort_as_half(b)) * FP16_INV_SCALE;
+    }
+}
+
+// (value, index) ordering: larger value first, then lower index.
+struct Top2 {
+    uint32_t bv;
+    int32_t bi;       // INT32_MAX = none
+    long long sv;     // -1 = none
+};
+
+__device__ __forceinline__ void top2_push(Top2 &t, uint32_t v, int32_t j) {
+    if (t.bi == INT32_MAX || v > t.bv || (v == t.bv && j < t.bi)) {
+        if (t.bi != INT32_MAX) t.sv = max(t.sv, (long long)t.bv);
+        t.bv = v;
+        t.bi = j;
+    } else {
+        t.sv = max(t.sv, (long long)v);
+    }
+}
+
+__device__ __forceinline__ Top2 top2_merge(Top2 a, Top2 b) {
+    Top2 r;
+    bool a_wins = a.bi != INT32_MAX && (b.bi == INT32_MAX || a.bv > b.bv || (a.bv == b.bv && a.bi < b.bi));
+    Top2 w = a_wins ? a : b, l = a_wins ? b : a;
+    r.bv = w.bv;
+    r.bi = w.bi;
+    r.sv = max(w.sv, l.sv);
+    if (l.bi != INT32_MAX) r.sv = max(r.sv, (long long)l.bv);
+    return r;
+}
+
+__device__ __forceinline__ Top2 top2_shfl(Top2 t, int o) {
+    Top2 r;
+    r.bv = __shfl_xor_sync(0xffffffffu, t.bv, o);
+    r.bi = __shfl_xor_sync(0xffffffffu, t.bi, o);
+    r.sv = __shfl_xor_sync(0xffffffffu, t.sv, o);
+    return r;
+}
+
+// FP64 dot product of object rows [rb, re) with centroid j's master row
+// (binary search of each object term in the centroid's ascending terms).
+// Fixed lane assignment plus a butterfly reduction: deterministic, and every
+// lane returns the same value.
+__device__ double exact_score(const AssignParams &P, int64_t rb, int64_t re, int j, int lane) {
+    const int64_t cb = P.coff[j], ce = P.coff[j + 1];
+    double acc = 0.0;
+    for (int64_t h = rb + lane; h < re; h += 32) {
+        const int t = P.idx[h];
+        int64_t lo = cb, hi = ce;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (P.cterm[mid] < t) lo = mid + 1; else hi = mid;
+        }
+        if (lo < ce && P.cterm[lo] == t) acc += (double)P.val[h] * (double)P.cval[lo];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+__device__ __forceinline__ double error_bound(double x, int64_t n, double S, double eps, double eta) {
+    const double ur = 5.9604644775390625e-08;  // 2^-24
+    double c = ur * (1.0 + eps) + eps;
+    double a = (double)n * FIX_QUANTUM + (1.0 + ur) * eta * S;
+    return (c * x + a) / (1.0 - c) * (1.0 + 1e-12);
+}
+
+template <int T>
+__device__ __forceinline__ int block_inclusive_scan_int(int x, int *warp_s, int *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_s[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        constexpr int NW = T / 32;
+        int w = lane < NW ? warp_s[lane] : 0;
+        int winc = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, winc, o);
+            if (lane >= o) winc += y;
+        }
+        if (lane < NW) warp_s[lane] = winc - w;
+        if (lane == NW - 1) *total = winc;
+    }
+    __syncthreads();
+    return warp_s[warp] + inc;
+}
+
+template <int T, int PREC>
+__global__ void __launch_bounds__(T) assign_kernel(AssignParams P) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    constexpr int NW = T / 32;
+    const int kpad = (P.k + 3) & ~3;
+    uint32_t *rho = smem;
+    float *s_v = reinterpret_cast<float *>(smem + kpad);
+    int *s_start = reinterpret_cast<int *>(s_v + T);
+    int *s_pre = s_start + T;
+    __shared__ int warp_i[32];
+    __shared__ int s_total;
+    __shared__ long long s_obj;
+    __shared__ Top2 warp_t[NW];
+    __shared__ double warp_d[NW];
+    __shared__ int warp_j[NW];
+    __shared__ int s_winner;
+    __shared__ int s_flag;
+    __shared__ uint32_t s_thr;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int j = tid; j < kpad; j += T) rho[j] = 0u;
+    unsigned long long c_post = 0, c_filt = 0, c_sim = 0, c_resc = 0, c_cand = 0, c_chg = 0;
+    __syncthreads();
+
+    for (;;) {
+        if (tid == 0) s_obj = (long long)atomicAdd(&P.ctr->work, 1ull);
+        __syncthreads();
+        const int64_t i = s_obj;
+        if (i >= P.N) break;
+        const int64_t rb = P.row_ptr[i], re = P.row_ptr[i + 1];
+        const int32_t a_prev = P.labels_prev[i];
+        const uint32_t own_q = P.own[i];
+        const bool filt = P.icp && a_prev >= 0 && own_q != OWN_INVALID && P.lam_prev[a_prev] != 0;
+        const int n_mov = filt ? *P.n_mov : 0;
+
+        // ---- similarity scan (Algorithm 4, lines 7-13) ----
+        for (int64_t cb = rb; cb < re; cb += T) {
+            const int cn = (int)min((int64_t)T, re - cb);
+            int len = 0;
+            if (tid < cn) {
+                const int t = P.idx[cb + tid];
+                const int64_t o0 = P.if_off[t];
+                len = filt ? P.if_mf0[t] : (int)(P.if_off[t + 1] - o0);
+                s_v[tid] = P.val[cb + tid];
+                s_start[tid] = (int)o0;
+            }
+            const int incl = block_inclusive_scan_int<T>(len, warp_i, &s_total);
+            s_pre[tid] = incl;
+            __syncthreads();
+            const int L = s_total;
+            if (tid == 0) c_post += (unsigned long long)L;
+            int h = 0, beg = 0, end = s_pre[0], start = s_start[0];
+            float v = s_v[0];
+            for (int p0 = tid; p0 < L; p0 += 4 * T) {
+                int pos[4];
+                float vv[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int p = p0 + m * T;
+                    pos[m] = -1;
+                    if (p < L) {
+                        while (p >= end) {
+                            ++h;
+                            beg = end;
+                            end = s_pre[h];
+                            start = s_start[h];
+                            v = s_v[h];
+                        }
+                        pos[m] = start + (p - beg);
+                        vv[m] = v;
+                    }
+                }
+                int cc[4];
+                float uu[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    if (pos[m] >= 0) {
+                        cc[m] = __ldg(P.if_cid + pos[m]);
+                        uu[m] = load_u<PREC>(P.if_vals, pos[m]);
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    if (pos[m] >= 0) {
+                        const float prod = vv[m] * uu[m];
+                        atomicAdd(&rho[cc[m]], __float2uint_ru(prod * FIX_SCALE));
+                    }
+                }
+            }
+            __syncthreads();
+        }
+
+        // ---- argmax over the candidates (Algorithm 4, lines 14-16) ----
+        Top2 t;
+        t.bv = 0u;
+        t.bi = INT32_MAX;
+        t.sv = -1;
+        if (!filt) {
+            for (int j = tid; j < P.k; j += T) top2_push(t, rho[j], j);
+        } else {
+            for (int m = tid; m < n_mov; m += T) {
+                const int j = P.mov_list[m];
+                top2_push(t, rho[j], j);
+            }
+            if (tid == 0) top2_push(t, own_q, a_prev);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t = top2_merge(t, top2_shfl(t, o));
+        if (lane == 0) warp_t[warp] = t;
+        __syncthreads();
+        if (tid == 0) {
+            Top2 b = warp_t[0];
+            for (int w = 1; w < NW; ++w) b = top2_merge(b, warp_t[w]);
+            int flag = 0;
+            uint32_t thr = 0;
+            if (b.bv > 0u && b.sv >= 0) {
+                const double best = (double)b.bv * FIX_QUANTUM;
+                const double E = error_bound(best, re - rb, (double)P.sumv[i], P.eps, P.eta);
+                const double gap = (double)((long long)b.bv - b.sv) * FIX_QUANTUM;
+                if (gap <= 2.0 * E) {
+                    flag = 1;
+                    const double span = ceil(2.0 * E / FIX_QUANTUM);
+                    thr = span >= (double)b.bv ? 0u : b.bv - (uint32_t)span;
+                }
+            }
+            s_winner = b.bi;
+            s_flag = flag;
+            s_thr = thr;
+        }
+        __syncthreads();
+
+        // ---- exact re-score of the candidates inside the bound ----
+        if (s_flag) {
+            const uint32_t thr = s_thr;
+            double wbest = -1.0;
+            int wj = INT32_MAX;
+            int ncand = 0;
+            const int total = filt ? n_mov : P.k;
+            for (int base = warp * 32; base < total; base += T) {
+                const int m = base + lane;
+                int j = -1;
+                if (m < total) {
+                    j = filt ? P.mov_list[m] : m;
+                    if (rho[j] < thr) j = -1;
+                }
+                unsigned bal = __ballot_sync(0xffffffffu, j >= 0);
+                while (bal) {
+                    const int src = __ffs(bal) - 1;
+                    bal &= bal - 1;
+                    const int jc = __shfl_sync(0xffffffffu, j, src);
+                    const double x = exact_score(P, rb, re, jc, lane);
+                    ++ncand;
+                    if (x > wbest || (x == wbest && jc < wj)) {
+                        wbest = x;
+                        wj = jc;
+                    }
+                }
+            }
+            if (filt && warp == 0 && own_q >= thr) {
+                const double x = exact_score(P, rb, re, a_prev, lane);
+                ++ncand;
+                if (x > wbest || (x == wbest && a_prev < wj)) {
+                    wbest = x;
+                    wj = a_prev;
+                }
+            }
+            if (lane == 0) {
+                warp_d[warp] = wbest;
+                warp_j[warp] = wj;
+                c_cand += (unsigned long long)ncand;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double bb = warp_d[0];
+                int bj = warp_j[0];
+                for (int w = 1; w < NW; ++w) {
+                    if (warp_d[w] > bb || (warp_d[w] == bb && warp_j[w] < bj)) {
+                        bb = warp_d[w];
+                        bj = warp_j[w];
+                    }
+                }
+                if (bj != INT32_MAX) s_winner = bj;
+                c_resc += 1;
+            }
+            __syncthreads();
+        }
+
+        // ---- write the assignment, mark moving clusters (lines 17-19) ----
+        if (tid == 0) {
+            const int a = s_winner;
+            P.labels[i] = a;
+            P.own[i] = (filt && a == a_prev) ? own_q : rho[a];
+            if (a != a_prev) {
+                c_chg += 1;
+                P.moving[a] = 1;
+                if (a_prev >= 0) P.moving[a_prev] = 1;
+            }
+            c_filt += filt ? 1ull : 0ull;
+            c_sim += filt ? (unsigned long long)n_mov : (unsigned long long)P.k;
+        }
+        __syncthreads();
+        if (!filt) {
+            for (int j = tid; j < P.k; j += T) rho[j] = 0u;
+        } else {
+            for (int m = tid; m < n_mov; m += T) rho[P.mov_list[m]] = 0u;
+        }
+        __syncthreads();
+    }
+
+    if (tid == 0) {
+        atomicAdd(&P.ctr->postings, c_post);
+        atomicAdd(&P.ctr->filtered, c_filt);
+        atomicAdd(&P.ctr->simcalc, c_sim);
+        atomicAdd(&P.ctr->changed, c_chg);
+    }
+    if (lane == 0 && (c_resc | c_cand)) {
+        atomicAdd(&P.ctr->rescored, c_resc);
+        atomicAdd(&P.ctr->rescore_cands, c_cand);
+    }
+}
+
+// lambda^[r] from the moving flags, and the ascending list of moving ids.
+__global__ void __launch_bounds__(1024) finalize_kernel(int32_t k, int first_iter, const uint8_t *moving,
+                                                        uint8_t *lam, int32_t *mov_list, int32_t *n_mov,
+                                                        DevCounters *ctr) {
+    __shared__ int warp_s[32];
+    __shared__ int total;
+    int carry = 0;
+    for (int b = 0; b < k; b += 1024) {
+        const int j = b + threadIdx.x;
+        int mv = 0;
+        if (j < k) {
+            mv = first_iter ? 1 : (moving[j] != 0);
+            lam[j] = mv ? 0 : 1;
+        }
+        const int incl = block_inclusive_scan_int<1024>(mv, warp_s, &total);
+        if (mv) mov_list[carry + incl - 1] = j;
+        carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *n_mov = carry;
+        ctr->n_moving = (unsigned long long)carry;
+    }
+}
+
+template <int T, int PREC>
+cudaError_t launch_t(sivf_ctx *c, const AssignParams &P, int ctas_per_sm) {
+    const int kpad = (c->k + 3) & ~3;
+    const size_t smem = (size_t)kpad * 4 + (size_t)T * 12;
+    auto kern = assign_kernel<T, PREC>;
+    SIVF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    SIVF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, smem));
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    int per_sm = ctas_per_sm > 0 ? min(ctas_per_sm, occ) : occ;
+    const int64_t grid64 = min((int64_t)c->num_sms * per_sm, c->N);
+    kern<<<(unsigned)grid64, T, smem, c->stream>>>(P);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_prec(sivf_ctx *c, const AssignParams &P) {
+    const int T = c->assign_threads;
+    const int cps = c->assign_ctas_per_sm;
+    switch (T) {
+        case 64: return launch_t<64, PREC>(c, P, cps);
+        case 128: return launch_t<128, PREC>(c, P, cps);
+        case 256: return launch_t<256, PREC>(c, P, cps);
+        case 512: return launch_t<512, PREC>(c, P, cps);
+        default: return launch_t<1024, PREC>(c, P, cps);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_assign(sivf_ctx *c) {
+    AssignParams P;
+    P.N = c->N;
+    P.k = c->k;
+    P.icp = c->cfg.icp;
+    P.row_ptr = c->row_ptr;
+    P.idx = c->idx;
+    P.val = c->val;
+    P.sumv = c->sumv;
+    P.if_off = c->if_off;
+    P.if_mf0 = c->if_mf0;
+    P.if_cid = c->if_cid;
+    P.if_vals = c->cfg.prec == SIVF_FP32 ? (const void *)c->if_val : (const void *)c->if_lp;
+    P.coff = c->coff[c->cur];
+    P.cterm = c->cterm[c->cur];
+    P.cval = c->cval[c->cur];
+    P.labels_prev = c->labels_prev;
+    P.labels = c->labels;
+    P.own = c->own;
+    P.lam_prev = c->lam_prev;
+    P.mov_list = c->mov_list;
+    P.n_mov = c->n_mov_dev;
+    P.moving = c->moving;
+    P.ctr = c->ctr;
+    if (c->cfg.prec == SIVF_BF16) {
+        P.eps = 0.00390625;  // 2^-8: bf16 keeps 8 significant bits
+        P.eta = 0.0;
+    } else if (c->cfg.prec == SIVF_FP16) {
+        P.eps = 0.00048828125;       // 2^-11
+        P.eta = 3.637978807091713e-12;  // 2^-38: subnormal spacing of u * 2^14, clamped away from 0
+    } else {
+        P.eps = 0.0;
+        P.eta = 0.0;
+    }
+    switch (c->cfg.prec) {
+        case SIVF_BF16: return launch_prec<SIVF_BF16>(c, P);
+        case SIVF_FP16: return launch_prec<SIVF_FP16>(c, P);
+        default: return launch_prec<SIVF_FP32>(c, P);
+    }
+}
+
+cudaError_t launch_finalize_assign(sivf_ctx *c) {
+    finalize_kernel<<<1, 1024, 0, c->stream>>>(c->k, c->iter == 1 ? 1 : 0, c->moving, c->lam, c->mov_list,
+                                               c->n_mov_dev, c->ctr);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace sivf

@@ -1,0 +1,237 @@
+// Device-wide primitives used by the update step: exclusive prefix sums and a
+// stable LSD radix sort of (uint32 key, uint32 value) pairs.
+//
+// Scan: reduce-then-scan in three launches (tile sums, one-CTA scan of the
+// tile sums, tile-local scan plus carry-in).
+// Radix sort: 8-bit digits, per pass (1) per-tile digit histograms stored
+// digit-major, (2) an exclusive scan of that table, (3) a stable scatter
+// whose in-tile ranks come from warp-level __match_any_sync on the digit.
+#include "sivf_internal.cuh"
+
+namespace sivf {
+
+unsigned long long g_launches = 0;
+
+int bits_for(uint64_t max_value) {
+    int b = 0;
+    while (b < 64 && (max_value >> b) != 0) ++b;
+    return b;
+}
+
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+template <typename T>
+__device__ T block_exclusive_scan(T x, T *smem_warp, T *block_total) {
+    // x: this thread's value; returns exclusive prefix within the block.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) smem_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        T w = lane < nw ? smem_warp[lane] : T(0);
+        T winc = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, winc, o);
+            if (lane >= o) winc += y;
+        }
+        if (lane < nw) smem_warp[lane] = winc - w;
+        if (lane == nw - 1) *block_total = winc;
+    }
+    __syncthreads();
+    T r = smem_warp[warp] + inc - x;
+    return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SCAN_THREADS) scan_tile_sums(const T *in, int64_t n, T *tile_sums) {
+    __shared__ T warp_s[32];
+    __shared__ T total;
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i)
+        if (base + i < n) s += in[base + i];
+    block_exclusive_scan<T>(s, warp_s, &total);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) scan_single_block(T *data, int64_t n, T *total_out) {
+    __shared__ T warp_s[32];
+    __shared__ T total;
+    T carry = 0;
+    for (int64_t b = 0; b < n; b += blockDim.x) {
+        int64_t i = b + threadIdx.x;
+        T x = i < n ? data[i] : T(0);
+        T ex = block_exclusive_scan<T>(x, warp_s, &total);
+        if (i < n) data[i] = carry + ex;
+        carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total_out) *total_out = carry;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SCAN_THREADS) scan_tiles(const T *in, T *out, int64_t n, const T *tile_offs) {
+    __shared__ T warp_s[32];
+    __shared__ T total;
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    T v[SCAN_ITEMS];
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        v[i] = base + i < n ? in[base + i] : T(0);
+        s += v[i];
+    }
+    T ex = block_exclusive_scan<T>(s, warp_s, &total) + tile_offs[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        if (base + i < n) out[base + i] = ex;
+        ex += v[i];
+    }
+}
+
+template <typename T>
+cudaError_t scan_exclusive_impl(const T *in, T *out, int64_t n, T *total, Workspace &ws, cudaStream_t s) {
+    if (n <= 0) {
+        if (total) SIVF_CUDA_TRY(cudaMemsetAsync(total, 0, sizeof(T), s));
+        return cudaSuccess;
+    }
+    int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    size_t mark = ws.used;
+    T *sums = ws.take<T>((size_t)tiles);
+    if (!sums) return cudaErrorMemoryAllocation;
+    scan_tile_sums<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, sums);
+    scan_single_block<T><<<1, 1024, 0, s>>>(sums, tiles, total);
+    scan_tiles<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, sums);
+    note_launch(3);
+    ws.used = mark;
+    return cudaGetLastError();
+}
+
+// ---------------- radix sort ----------------
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 4096
+constexpr int RS_BITS = 8;
+constexpr int RS_RADIX = 1 << RS_BITS;
+
+__global__ void __launch_bounds__(RS_THREADS) radix_hist(const uint32_t *keys, int64_t n, int shift, uint32_t mask,
+                                                         uint32_t *counts, int64_t tiles) {
+    __shared__ uint32_t h[RS_RADIX];
+    for (int d = threadIdx.x; d < RS_RADIX; d += RS_THREADS) h[d] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
+        int64_t p = base + i;
+        if (p < n) atomicAdd(&h[(keys[p] >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < RS_RADIX; d += RS_THREADS) counts[(int64_t)d * tiles + blockIdx.x] = h[d];
+}
+
+__global__ void __launch_bounds__(RS_THREADS) radix_scatter(const uint32_t *__restrict__ kin,
+                                                            const uint32_t *__restrict__ vin,
+                                                            uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                            int64_t n, int shift, uint32_t mask,
+                                                            const uint32_t *__restrict__ offs, int64_t tiles) {
+    __shared__ uint32_t wcnt[RS_WARPS][RS_RADIX];
+    __shared__ uint32_t toff[RS_RADIX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < RS_RADIX; d += RS_THREADS) {
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) wcnt[w][d] = 0;
+        toff[d] = offs[(int64_t)d * tiles + blockIdx.x];
+    }
+    __syncthreads();
+    const int64_t wbase = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * (32 * RS_ITEMS);
+    uint32_t kk[RS_ITEMS], vv[RS_ITEMS], rk[RS_ITEMS];
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        int64_t p = wbase + r * 32 + lane;
+        bool valid = p < n;
+        uint32_t key = valid ? kin[p] : 0u;
+        kk[r] = key;
+        vv[r] = valid ? vin[p] : 0u;
+        uint32_t d = valid ? ((key >> shift) & mask) : (uint32_t)RS_RADIX;  // sentinel groups invalid lanes
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        uint32_t old = valid ? wcnt[warp][d] : 0u;
+        __syncwarp();
+        if (valid && (peers & lt) == 0) wcnt[warp][d] = old + (uint32_t)__popc(peers);
+        __syncwarp();
+        rk[r] = old + (uint32_t)__popc(peers & lt);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < RS_RADIX; d += RS_THREADS) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) {
+            uint32_t c = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        int64_t p = wbase + r * 32 + lane;
+        if (p < n) {
+            uint32_t d = (kk[r] >> shift) & mask;
+            uint32_t pos = toff[d] + wcnt[warp][d] + rk[r];
+            kout[pos] = kk[r];
+            vout[pos] = vv[r];
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total, Workspace &ws,
+                               cudaStream_t s) {
+    return scan_exclusive_impl<int64_t>(in, out, n, total, ws, s);
+}
+
+cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, Workspace &ws, cudaStream_t s) {
+    return scan_exclusive_impl<uint32_t>(in, out, n, nullptr, ws, s);
+}
+
+cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, int64_t n, int nbits,
+                             bool *result_in_alt, Workspace &ws, cudaStream_t s) {
+    *result_in_alt = false;
+    if (n <= 1 || nbits <= 0) return cudaSuccess;
+    if (n > (int64_t)0xFFFFFFFFll) return cudaErrorInvalidValue;
+    int64_t tiles = (n + RS_TILE - 1) / RS_TILE;
+    size_t mark = ws.used;
+    uint32_t *counts = ws.take<uint32_t>((size_t)tiles * RS_RADIX);
+    if (!counts) return cudaErrorMemoryAllocation;
+    uint32_t *ka = k0, *va = v0, *kb = k1, *vb = v1;
+    for (int shift = 0; shift < nbits; shift += RS_BITS) {
+        int w = nbits - shift < RS_BITS ? nbits - shift : RS_BITS;
+        uint32_t mask = (1u << w) - 1u;
+        radix_hist<<<(unsigned)tiles, RS_THREADS, 0, s>>>(ka, n, shift, mask, counts, tiles);
+        cudaError_t e = scan_exclusive_impl<uint32_t>(counts, counts, tiles * RS_RADIX, nullptr, ws, s);
+        if (e != cudaSuccess) return e;
+        radix_scatter<<<(unsigned)tiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, mask, counts, tiles);
+        note_launch(2);
+        uint32_t *t = ka; ka = kb; kb = t;
+        t = va; va = vb; vb = t;
+        *result_in_alt = !*result_in_alt;
+    }
+    ws.used = mark;
+    return cudaGetLastError();
+}
+
+}  // namespace sivf

@@ -1,0 +1,162 @@
+// Internal declarations of the SIVF GB300 library (not part of the C ABI).
+//
+// Data layout in HBM (all device arrays owned by the context unless noted):
+//   object CSR            row_ptr int64[N+1], idx int32[nnz], val f32[nnz]  (borrowed)
+//   labels, labels_prev   int32[N]      a^[r], a^[r-1]
+//   own                   uint32[N]     fixed-point (2^-31) score of the object's own
+//                                        cluster from its last scan; OWN_INVALID = none
+//   sumv                  f32[N]        sum of the object's values (error bound)
+//   lam, lam_prev         uint8[k]      lambda^[r], lambda^[r-1] (1 = invariant)
+//   mov_list              int32[k]      ids j with lambda^[r] = 0 (ascending)
+//   centroids (x2)        coff int64[k+1], cterm int32[cap], cval f32[cap], cclu int32[cap]
+//                                        cluster-major FP32 master copy, ascending terms
+//   snorm                 f64[k]        ||s_j|| of the sum behind each centroid
+//   inverted file         if_off int64[D+1], if_mf0 int32[D], if_cid int32[cap],
+//                                        if_val f32[cap], if_lp u16[cap] (bf16/fp16 copy)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "sivf.h"
+
+namespace sivf {
+
+constexpr uint32_t OWN_INVALID = 0xFFFFFFFFu;
+// Scores are accumulated as unsigned fixed point with quantum 2^-31:
+// q = ceil(fl(v * u) * 2^31). Cosine scores are <= 1 (+ rounding), so the
+// sum of an object's terms stays below 2^32.
+constexpr float FIX_SCALE = 2147483648.0f;  // 2^31
+constexpr double FIX_QUANTUM = 4.656612873077392578125e-10;  // 2^-31
+// FP16 postings store u * 2^14 so that every centroid value >= 2^-28 is a
+// normal half-precision number.
+constexpr float FP16_SCALE = 16384.0f;
+constexpr float FP16_INV_SCALE = 1.0f / 16384.0f;
+
+struct DevCounters {
+    unsigned long long changed;
+    unsigned long long filtered;
+    unsigned long long simcalc;
+    unsigned long long postings;
+    unsigned long long rescored;
+    unsigned long long rescore_cands;
+    unsigned long long n_moving;     // lambda^[r] = 0 count (written by finalize)
+    unsigned long long work;         // object work counter of the assignment kernel
+    unsigned long long error;        // nonzero: device-side check failed (code)
+    unsigned long long pad[7];
+};
+
+// Bump allocator over one device block (scratch that lives for one step).
+struct Workspace {
+    char *base = nullptr;
+    size_t cap = 0, used = 0;
+    void reset() { used = 0; }
+    template <typename T>
+    T *take(size_t n) {
+        size_t bytes = (n * sizeof(T) + 255) & ~size_t(255);
+        if (used + bytes > cap) return nullptr;
+        T *p = reinterpret_cast<T *>(base + used);
+        used += bytes;
+        return p;
+    }
+};
+
+}  // namespace sivf
+
+struct sivf_ctx {
+    sivf_config cfg;
+    int64_t N = 0;
+    int32_t D = 0, k = 0;
+    int64_t nnz = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    const int64_t *row_ptr = nullptr;
+    const int32_t *idx = nullptr;
+    const float *val = nullptr;
+
+    bool latched = false;
+    bool needs_update = false;  // an assignment or set_labels since the last update
+    std::string err;
+    int32_t iter = 0;
+    int bits_t = 0;  // bits of a term id
+
+    // object state
+    int32_t *labels = nullptr, *labels_prev = nullptr;
+    uint32_t *own = nullptr;
+    float *sumv = nullptr;
+
+    // cluster state
+    uint8_t *lam = nullptr, *lam_prev = nullptr, *moving = nullptr;
+    int32_t *mov_list = nullptr;
+    int32_t *n_mov_dev = nullptr;
+    double *snorm = nullptr, *snorm_new = nullptr;
+
+    // centroids, double-buffered
+    int64_t *coff[2] = {nullptr, nullptr};
+    int32_t *cterm[2] = {nullptr, nullptr};
+    float *cval[2] = {nullptr, nullptr};
+    int32_t *cclu = nullptr;  // cluster id of each entry of the current buffer
+    int cur = 0;
+    int64_t cap_c = 0;
+    int64_t c_nnz = 0;
+
+    // structured inverted file
+    int64_t *if_off = nullptr;
+    int32_t *if_mf0 = nullptr;
+    int32_t *if_cid = nullptr;
+    float *if_val = nullptr;
+    uint16_t *if_lp = nullptr;
+    int64_t if_nnz = 0;
+
+    // counters and step scratch
+    sivf::DevCounters *ctr = nullptr;
+    sivf::DevCounters *ctr_host = nullptr;  // pinned mirror
+    double *obj_dev = nullptr;              // [2]: J_assign, J_update
+    sivf::Workspace ws;
+    size_t ws_bytes = 0;
+    size_t owned_bytes = 0;
+    sivf_stats stats{};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int assign_threads = 0, assign_ctas_per_sm = 0;
+    unsigned long long launch_base = 0;  // g_launches at init / reseed
+};
+
+namespace sivf {
+
+// Kernel launches issued by the library (host-side count, all contexts).
+extern unsigned long long g_launches;
+inline void note_launch(unsigned long long n = 1) { __atomic_fetch_add(&g_launches, n, __ATOMIC_RELAXED); }
+
+// ---- primitives.cu ----
+// Exclusive prefix sum of n elements (in may equal out). Optional total.
+cudaError_t scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total, Workspace &ws,
+                               cudaStream_t s);
+cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, Workspace &ws, cudaStream_t s);
+// Stable LSD radix sort of (key, value) pairs on the low `nbits` bits of the
+// keys. Input in (k0, v0); (k1, v1) is scratch of the same size. Returns, via
+// *result_in_alt, whether the sorted output ended in (k1, v1).
+cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, int64_t n, int nbits,
+                             bool *result_in_alt, Workspace &ws, cudaStream_t s);
+int bits_for(uint64_t max_value);  // number of bits to hold values in [0, max_value]
+
+// ---- assign.cu ----
+cudaError_t launch_assign(sivf_ctx *c);
+cudaError_t launch_finalize_assign(sivf_ctx *c);
+
+// ---- update.cu ----
+cudaError_t run_update(sivf_ctx *c);
+cudaError_t build_inverted_file(sivf_ctx *c);
+cudaError_t validate_csr(sivf_ctx *c, int *bad);
+cudaError_t init_centroids(sivf_ctx *c, const int32_t *init_ids_dev);
+cudaError_t set_labels_dev(sivf_ctx *c, const int32_t *src_dev);
+cudaError_t reseed_dev(sivf_ctx *c, const int32_t *init_ids_dev);
+
+}  // namespace sivf
+
+#define SIVF_CUDA_TRY(expr)                    \
+    do {                                       \
+        cudaError_t e__ = (expr);              \
+        if (e__ != cudaSuccess) return e__;    \
+    } while (0)

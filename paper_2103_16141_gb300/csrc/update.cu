@@ -1,0 +1,547 @@
+// Update step of SIVF (Algorithm 5, Section 4.2) on sm_103a, plus the
+// set-up kernels (CSR validation, seed centroids).
+//
+// Pipeline for iteration r (lambda = lambda^[r] from the assignment):
+//  u1  stable radix sort of (label, object id): members of each cluster in
+//      ascending object id; per-cluster member counts.
+//  u2  for every moving, non-empty cluster ("recomputed"), expand its members'
+//      (term, value) pairs in member order, stable-sort them by
+//      (cluster rank, term) and reduce equal keys sequentially in FP64. The sum
+//      of each (cluster, term) therefore accumulates in ascending object id,
+//      the order of the plain definition (Algorithm 5, lines 17-20), and is
+//      reproducible bit for bit.
+//  u3  ||s_j|| in FP64 (fixed reduction tree), u = s / ||s|| stored as FP32
+//      (dividing by |C_j| first cancels exactly and is skipped); the objective
+//      pieces sum_j <s_j, mu_j^[r-1]> and sum_j ||s_j||.
+//  u4  invariant and empty clusters keep their centroid row (copied).
+//  u5  structured inverted file: stable radix sort of the centroid entries by
+//      (term, lambda_j); the cluster-major input is in ascending j, so each
+//      term's list holds the moving centroids first and the invariant ones
+//      after, ascending ids in each part (Algorithm 5, lines 1-14 and 21-30).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "sivf_internal.cuh"
+
+namespace sivf {
+namespace {
+
+constexpr int TPB = 256;
+
+inline unsigned blocks_for(int64_t n, int tpb = TPB) {
+    int64_t b = (n + tpb - 1) / tpb;
+    if (b < 1) b = 1;
+    if (b > 0x7FFFFFFF) b = 0x7FFFFFFF;
+    return (unsigned)b;
+}
+
+// ---------------- validation and set-up ----------------
+
+// bad bits: 1 row_ptr, 2 idx range/order, 4 value, 8 norm
+__global__ void k_validate(int64_t N, int32_t D, int64_t nnz, const int64_t *row_ptr, const int32_t *idx,
+                           const float *val, float *sumv, int *bad) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = wid; i < N; i += nw) {
+        const int64_t b = row_ptr[i], e = row_ptr[i + 1];
+        int flags = 0;
+        if (b < 0 || e < b || e > nnz) flags |= 1;
+        double ss = 0.0, sv = 0.0;
+        if (!(flags & 1)) {
+            for (int64_t h = b + lane; h < e; h += 32) {
+                const int t = idx[h];
+                const float v = val[h];
+                if (t < 0 || t >= D) flags |= 2;
+                if (h > b && idx[h - 1] >= t) flags |= 2;
+                if (!(v > 0.0f) || !isfinite(v)) flags |= 4;
+                ss += (double)v * (double)v;
+                sv += (double)v;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            sv += __shfl_xor_sync(0xffffffffu, sv, o);
+            flags |= __shfl_xor_sync(0xffffffffu, flags, o);
+        }
+        if (lane == 0) {
+            if (!(flags & 1) && e > b && fabs(sqrt(ss) - 1.0) > 1e-4) flags |= 8;
+            sumv[i] = (float)(sv * (1.0 + 1e-6));  // rounded up: the bound needs S >= sum v
+            if (flags) atomicOr(bad, flags);
+        }
+    }
+}
+
+__global__ void k_seed_sizes(int32_t k, const int32_t *init_ids, const int64_t *row_ptr, int64_t *sz) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < k) {
+        int64_t d = init_ids[j];
+        sz[j] = row_ptr[d + 1] - row_ptr[d];
+    }
+}
+
+__global__ void k_seed_rows(int32_t k, const int32_t *init_ids, const int64_t *row_ptr, const int32_t *idx,
+                            const float *val, const int64_t *coff, int32_t *cterm, float *cval, int32_t *cclu) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (wid >= k) return;
+    const int j = (int)wid;
+    const int64_t d = init_ids[j];
+    const int64_t b = row_ptr[d], e = row_ptr[d + 1], o = coff[j];
+    for (int64_t h = b + lane; h < e; h += 32) {
+        cterm[o + (h - b)] = idx[h];
+        cval[o + (h - b)] = val[h];
+        cclu[o + (h - b)] = j;
+    }
+}
+
+// Replace a^[r] by src. lambda^[r] is recomputed against a^[r-1] (every
+// cluster moving before the second assignment); an object whose label
+// changes loses its stored own-cluster score.
+__global__ void k_set_labels(int64_t N, const int32_t *src, int32_t *labels, const int32_t *labels_prev,
+                             uint32_t *own, uint8_t *moving) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = src[i];
+        if (labels[i] != a) {
+            labels[i] = a;
+            own[i] = OWN_INVALID;
+        }
+        const int32_t prev = labels_prev[i];
+        if (a != prev) {
+            moving[a] = 1;
+            if (prev >= 0) moving[prev] = 1;
+        }
+    }
+}
+
+__global__ void k_check_labels(int64_t N, int32_t k, const int32_t *src, int *bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = src[i];
+        if (a < 0 || a >= k) atomicOr(bad, 1);
+    }
+}
+
+// ---------------- u1: group objects by label ----------------
+
+__global__ void k_label_keys(int64_t N, const int32_t *labels, uint32_t *keys, uint32_t *vals, int64_t *cnt) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = labels[i];
+        keys[i] = (uint32_t)a;
+        vals[i] = (uint32_t)i;
+        atomicAdd(reinterpret_cast<unsigned long long *>(cnt + a), 1ull);
+    }
+}
+
+// recompute flag: moving (lambda = 0) and non-empty
+__global__ void k_recompute_flags(int32_t k, const uint8_t *lam, const int64_t *cnt, int64_t *flag) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < k) flag[j] = (lam[j] == 0 && cnt[j] > 0) ? 1 : 0;
+}
+
+// ---------------- u2: cluster sums ----------------
+
+__global__ void k_member_tuples(int64_t N, const uint32_t *perm, const int32_t *labels, const int64_t *flag,
+                                const int64_t *rrank, int64_t r0, int64_t r1, const int64_t *row_ptr,
+                                int64_t *tc) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = perm[p];
+        const int32_t j = labels[i];
+        int64_t n = 0;
+        if (flag[j]) {
+            const int64_t r = rrank[j];
+            if (r >= r0 && r < r1) n = row_ptr[i + 1] - row_ptr[i];
+        }
+        tc[p] = n;
+    }
+}
+
+__global__ void k_expand(int64_t N, const uint32_t *perm, const int32_t *labels, const int64_t *rrank,
+                         int64_t r0, const int64_t *tc, const int64_t *toff, const int64_t *row_ptr,
+                         const int32_t *idx, const float *val, int bits_t, uint32_t *keys, uint32_t *vals) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = wid; p < N; p += nw) {
+        if (tc[p] == 0) continue;
+        const int64_t i = perm[p];
+        const uint32_t rk = (uint32_t)(rrank[labels[i]] - r0);
+        const int64_t b = row_ptr[i], e = row_ptr[i + 1], o = toff[p];
+        for (int64_t h = b + lane; h < e; h += 32) {
+            keys[o + (h - b)] = (rk << bits_t) | (uint32_t)idx[h];
+            vals[o + (h - b)] = __float_as_uint(val[h]);
+        }
+    }
+}
+
+__global__ void k_heads(int64_t n, const uint32_t *keys, int64_t *head) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        head[e] = (e == 0 || keys[e] != keys[e - 1]) ? 1 : 0;
+}
+
+// sequential FP64 sum of each run of equal keys, in input (ascending object) order
+__global__ void k_segsum(int64_t n, const uint32_t *keys, const uint32_t *vals, const int64_t *uidx, int64_t ubase,
+                         int bits_t, int64_t r0, int32_t *uterm, double *usum, int64_t *sup) {
+    const uint32_t tmask = (1u << bits_t) - 1u;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = keys[e];
+        if (e > 0 && keys[e - 1] == key) continue;
+        double s = 0.0;
+        for (int64_t f = e; f < n && keys[f] == key; ++f) s += (double)__uint_as_float(vals[f]);
+        const int64_t u = ubase + uidx[e];
+        uterm[u] = (int32_t)(key & tmask);
+        usum[u] = s;
+        atomicAdd(reinterpret_cast<unsigned long long *>(sup + r0 + (key >> bits_t)), 1ull);
+    }
+}
+
+// ---------------- u3 / u4: new centroid rows ----------------
+
+__global__ void k_new_sizes(int32_t k, const int64_t *flag, const int64_t *rrank, const int64_t *sup,
+                            const int64_t *coff_old, int64_t *sz) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < k) sz[j] = flag[j] ? sup[rrank[j]] : coff_old[j + 1] - coff_old[j];
+}
+
+__global__ void k_write_rows(int32_t k, const int64_t *flag, const int64_t *rrank, const int64_t *supoff,
+                             const int64_t *sup, const int32_t *uterm, const double *usum, const int64_t *cnt,
+                             const int64_t *coff_old, const int32_t *cterm_old, const float *cval_old,
+                             const double *snorm_old, const int64_t *coff_new, int32_t *cterm_new, float *cval_new,
+                             int32_t *cclu_new, double *snorm_new, double *jA, double *jU) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (wid >= k) return;
+    const int j = (int)wid;
+    const int64_t o = coff_new[j];
+    if (flag[j]) {
+        const int64_t r = rrank[j];
+        const int64_t ub = supoff[r], n = sup[r];
+        double ss = 0.0;
+        for (int64_t q = lane; q < n; q += 32) ss += usum[ub + q] * usum[ub + q];
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, s);
+        const double nrm = sqrt(ss);
+        // <s_j, mu_j^[r-1]>: binary search of each term in the previous row
+        const int64_t cb = coff_old[j], ce = coff_old[j + 1];
+        double dot = 0.0;
+        for (int64_t q = lane; q < n; q += 32) {
+            const int32_t t = uterm[ub + q];
+            const double sv = usum[ub + q];
+            cterm_new[o + q] = t;
+            cval_new[o + q] = (float)(sv / nrm);
+            cclu_new[o + q] = j;
+            int64_t lo = cb, hi = ce;
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                if (cterm_old[mid] < t) lo = mid + 1; else hi = mid;
+            }
+            if (lo < ce && cterm_old[lo] == t) dot += sv * (double)cval_old[lo];
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, s);
+        if (lane == 0) {
+            snorm_new[j] = nrm;
+            jA[j] = dot;
+            jU[j] = nrm;
+        }
+    } else {
+        const int64_t cb = coff_old[j], ce = coff_old[j + 1];
+        for (int64_t q = cb + lane; q < ce; q += 32) {
+            cterm_new[o + (q - cb)] = cterm_old[q];
+            cval_new[o + (q - cb)] = cval_old[q];
+            cclu_new[o + (q - cb)] = j;
+        }
+        if (lane == 0) {
+            const double sn = cnt[j] > 0 ? snorm_old[j] : 0.0;
+            snorm_new[j] = sn;
+            jA[j] = sn;  // unchanged members: <s_j, s_j / ||s_j||> = ||s_j||
+            jU[j] = sn;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_sum2(int32_t k, const double *a, const double *b, double *out) {
+    // fixed-order reduction: per-thread strided partial sums, then a tree
+    __shared__ double sa[1024], sb[1024];
+    double x = 0.0, y = 0.0;
+    for (int j = threadIdx.x; j < k; j += 1024) {
+        x += a[j];
+        y += b[j];
+    }
+    sa[threadIdx.x] = x;
+    sb[threadIdx.x] = y;
+    __syncthreads();
+    for (int s = 512; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            sa[threadIdx.x] += sa[threadIdx.x + s];
+            sb[threadIdx.x] += sb[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sa[0];
+        out[1] = sb[0];
+    }
+}
+
+// ---------------- u5: structured inverted file ----------------
+
+__global__ void k_if_keys(int64_t n, const int32_t *cterm, const int32_t *cclu, const uint8_t *lam, uint32_t *keys,
+                          uint32_t *vals, uint32_t *cnt2) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = ((uint32_t)cterm[e] << 1) | (uint32_t)(lam[cclu[e]] ? 1 : 0);
+        keys[e] = key;
+        vals[e] = (uint32_t)e;
+        atomicAdd(cnt2 + key, 1u);
+    }
+}
+
+__global__ void k_if_lens(int32_t D, const uint32_t *cnt2, int64_t *len, int32_t *mf0) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < D) {
+        len[t] = (int64_t)cnt2[2 * t] + (int64_t)cnt2[2 * t + 1];
+        mf0[t] = (int32_t)cnt2[2 * t];
+    }
+}
+
+__global__ void k_if_fill(int64_t n, const uint32_t *order, const int32_t *cclu, const float *cval, int prec,
+                          int32_t *if_cid, float *if_val, uint16_t *if_lp) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t e = order[q];
+        const float u = cval[e];
+        if_cid[q] = cclu[e];
+        if_val[q] = u;
+        if (prec == SIVF_BF16) {
+            if_lp[q] = __bfloat16_as_ushort(__float2bfloat16_rn(u));
+        } else if (prec == SIVF_FP16) {
+            unsigned short h = __half_as_ushort(__float2half_rn(u * FP16_SCALE));
+            if (h == 0 && u > 0.0f) h = 1;  // keep every posting strictly positive
+            if_lp[q] = h;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t validate_csr(sivf_ctx *c, int *bad_host) {
+    int *bad = c->ws.take<int>(1);
+    if (!bad) return cudaErrorMemoryAllocation;
+    SIVF_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+    k_validate<<<blocks_for(c->N * 32), TPB, 0, c->stream>>>(c->N, c->D, c->nnz, c->row_ptr, c->idx, c->val,
+                                                               c->sumv, bad);
+    note_launch();
+    SIVF_CUDA_TRY(cudaGetLastError());
+    SIVF_CUDA_TRY(cudaMemcpyAsync(bad_host, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    SIVF_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->ws.reset();
+    return cudaSuccess;
+}
+
+cudaError_t init_centroids(sivf_ctx *c, const int32_t *init_ids_dev) {
+    const int cur = c->cur;
+    int64_t *sz = c->ws.take<int64_t>((size_t)c->k + 1);
+    int64_t *total = c->ws.take<int64_t>(1);
+    if (!sz || !total) return cudaErrorMemoryAllocation;
+    k_seed_sizes<<<blocks_for(c->k), TPB, 0, c->stream>>>(c->k, init_ids_dev, c->row_ptr, sz);
+    note_launch();
+    SIVF_CUDA_TRY(scan_exclusive_i64(sz, c->coff[cur], c->k, total, c->ws, c->stream));
+    SIVF_CUDA_TRY(cudaMemcpyAsync(c->coff[cur] + c->k, total, sizeof(int64_t), cudaMemcpyDeviceToDevice, c->stream));
+    int64_t tot = 0;
+    SIVF_CUDA_TRY(cudaMemcpyAsync(&tot, total, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    SIVF_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (tot > c->cap_c) return cudaErrorMemoryAllocation;
+    c->c_nnz = tot;
+    k_seed_rows<<<blocks_for((int64_t)c->k * 32), TPB, 0, c->stream>>>(c->k, init_ids_dev, c->row_ptr, c->idx,
+                                                                       c->val, c->coff[cur], c->cterm[cur],
+                                                                       c->cval[cur], c->cclu);
+    note_launch();
+    SIVF_CUDA_TRY(cudaGetLastError());
+    SIVF_CUDA_TRY(cudaMemsetAsync(c->snorm, 0, sizeof(double) * c->k, c->stream));
+    c->ws.reset();
+    return cudaSuccess;
+}
+
+cudaError_t set_labels_dev(sivf_ctx *c, const int32_t *src) {
+    // src must not live in the workspace region taken below
+    int *bad = c->ws.take<int>(1);
+    if (!bad) return cudaErrorMemoryAllocation;
+    SIVF_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+    k_check_labels<<<blocks_for(c->N), TPB, 0, c->stream>>>(c->N, c->k, src, bad);
+    note_launch();
+    int bad_h = 0;
+    SIVF_CUDA_TRY(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    SIVF_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (bad_h) return cudaErrorInvalidValue;
+    SIVF_CUDA_TRY(cudaMemsetAsync(c->moving, 0, c->k, c->stream));
+    k_set_labels<<<blocks_for(c->N), TPB, 0, c->stream>>>(c->N, src, c->labels, c->labels_prev, c->own, c->moving);
+    note_launch();
+    SIVF_CUDA_TRY(cudaGetLastError());
+    if (c->iter == 0) c->iter = 1;  // first membership: every cluster is moving
+    SIVF_CUDA_TRY(launch_finalize_assign(c));
+    return cudaSuccess;
+}
+
+// Restart from new seeds: no labels, no own scores, every cluster moving,
+// mu^[0] = seed rows, first inverted file.
+cudaError_t reseed_dev(sivf_ctx *c, const int32_t *init_ids_dev) {
+    const int64_t N = c->N;
+    const int32_t k = c->k;
+    SIVF_CUDA_TRY(cudaMemsetAsync(c->labels, 0xFF, sizeof(int32_t) * N, c->stream));
+    SIVF_CUDA_TRY(cudaMemsetAsync(c->labels_prev, 0xFF, sizeof(int32_t) * N, c->stream));
+    SIVF_CUDA_TRY(cudaMemsetAsync(c->own, 0xFF, sizeof(uint32_t) * N, c->stream));
+    SIVF_CUDA_TRY(cudaMemsetAsync(c->lam, 0, k, c->stream));
+    SIVF_CUDA_TRY(cudaMemsetAsync(c->lam_prev, 0, k, c->stream));
+    SIVF_CUDA_TRY(cudaMemsetAsync(c->moving, 1, k, c->stream));
+    SIVF_CUDA_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream));
+    c->iter = 1;  // finalize below marks every cluster moving
+    SIVF_CUDA_TRY(launch_finalize_assign(c));
+    c->iter = 0;
+    SIVF_CUDA_TRY(init_centroids(c, init_ids_dev));
+    SIVF_CUDA_TRY(build_inverted_file(c));
+    c->needs_update = false;
+    return cudaSuccess;
+}
+
+cudaError_t build_inverted_file(sivf_ctx *c) {
+    const int64_t n = c->c_nnz;
+    const int cur = c->cur;
+    Workspace &ws = c->ws;
+    size_t mark = ws.used;
+    uint32_t *cnt2 = ws.take<uint32_t>((size_t)2 * c->D);
+    int64_t *len = ws.take<int64_t>((size_t)c->D + 1);
+    int64_t *total = ws.take<int64_t>(1);
+    uint32_t *k0 = ws.take<uint32_t>((size_t)n + 1), *v0 = ws.take<uint32_t>((size_t)n + 1);
+    uint32_t *k1 = ws.take<uint32_t>((size_t)n + 1), *v1 = ws.take<uint32_t>((size_t)n + 1);
+    if (!cnt2 || !len || !total || !k0 || !v0 || !k1 || !v1) return cudaErrorMemoryAllocation;
+    SIVF_CUDA_TRY(cudaMemsetAsync(cnt2, 0, sizeof(uint32_t) * 2 * c->D, c->stream));
+    if (n > 0) {
+        k_if_keys<<<blocks_for(n), TPB, 0, c->stream>>>(n, c->cterm[cur], c->cclu, c->lam, k0, v0, cnt2);
+        note_launch();
+    }
+    k_if_lens<<<blocks_for(c->D), TPB, 0, c->stream>>>(c->D, cnt2, len, c->if_mf0);
+    note_launch();
+    SIVF_CUDA_TRY(cudaGetLastError());
+    SIVF_CUDA_TRY(scan_exclusive_i64(len, c->if_off, c->D, total, ws, c->stream));
+    SIVF_CUDA_TRY(cudaMemcpyAsync(c->if_off + c->D, total, sizeof(int64_t), cudaMemcpyDeviceToDevice, c->stream));
+    bool alt = false;
+    SIVF_CUDA_TRY(radix_sort_pairs(k0, v0, k1, v1, n, c->bits_t + 1, &alt, ws, c->stream));
+    if (n > 0) {
+        k_if_fill<<<blocks_for(n), TPB, 0, c->stream>>>(n, alt ? v1 : v0, c->cclu, c->cval[cur], (int)c->cfg.prec,
+                                                       c->if_cid, c->if_val, c->if_lp);
+        note_launch();
+    }
+    SIVF_CUDA_TRY(cudaGetLastError());
+    c->if_nnz = n;
+    ws.used = mark;
+    return cudaSuccess;
+}
+
+cudaError_t run_update(sivf_ctx *c) {
+    cudaStream_t s = c->stream;
+    Workspace &ws = c->ws;
+    ws.reset();
+    const int64_t N = c->N;
+    const int32_t k = c->k;
+    const int old = c->cur, nw = 1 - c->cur;
+
+    // u1: members grouped by cluster, ascending object id
+    uint32_t *lk0 = ws.take<uint32_t>(N), *lv0 = ws.take<uint32_t>(N);
+    uint32_t *lk1 = ws.take<uint32_t>(N), *lv1 = ws.take<uint32_t>(N);
+    int64_t *cnt = ws.take<int64_t>(k), *flag = ws.take<int64_t>(k), *rrank = ws.take<int64_t>(k);
+    int64_t *nrec_d = ws.take<int64_t>(1), *tot_d = ws.take<int64_t>(1);
+    int64_t *sz = ws.take<int64_t>((size_t)k + 1);
+    double *jAd = ws.take<double>(k), *jUd = ws.take<double>(k);
+    int64_t *tc = ws.take<int64_t>(N), *toff = ws.take<int64_t>(N);
+    if (!lk0 || !lv0 || !lk1 || !lv1 || !cnt || !flag || !rrank || !nrec_d || !tot_d || !sz || !jAd || !jUd || !tc ||
+        !toff)
+        return cudaErrorMemoryAllocation;
+    SIVF_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * k, s));
+    k_label_keys<<<blocks_for(N), TPB, 0, s>>>(N, c->labels, lk0, lv0, cnt);
+    note_launch();
+    bool alt = false;
+    SIVF_CUDA_TRY(radix_sort_pairs(lk0, lv0, lk1, lv1, N, bits_for((uint64_t)(k - 1)), &alt, ws, s));
+    const uint32_t *perm = alt ? lv1 : lv0;
+    k_recompute_flags<<<blocks_for(k), TPB, 0, s>>>(k, c->lam, cnt, flag);
+    note_launch();
+    SIVF_CUDA_TRY(scan_exclusive_i64(flag, rrank, k, nrec_d, ws, s));
+    int64_t nrec = 0;
+    SIVF_CUDA_TRY(cudaMemcpyAsync(&nrec, nrec_d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SIVF_CUDA_TRY(cudaStreamSynchronize(s));
+
+    // u2: per (cluster, term) sums for the recomputed clusters, in rank batches
+    int64_t *sup = ws.take<int64_t>((size_t)nrec + 1), *supoff = ws.take<int64_t>((size_t)nrec + 1);
+    const int64_t ucap = c->nnz + 1;
+    int32_t *uterm = ws.take<int32_t>((size_t)ucap);
+    double *usum = ws.take<double>((size_t)ucap);
+    if (!sup || !supoff || !uterm || !usum) return cudaErrorMemoryAllocation;
+    SIVF_CUDA_TRY(cudaMemsetAsync(sup, 0, sizeof(int64_t) * (nrec + 1), s));
+    const int rbits_max = 32 - c->bits_t;
+    const int64_t batch = rbits_max >= 31 ? (int64_t)1 << 31 : (int64_t)1 << rbits_max;
+    int64_t ubase = 0, moved_nnz = 0;
+    for (int64_t r0 = 0; r0 < nrec; r0 += batch) {
+        const int64_t r1 = r0 + batch < nrec ? r0 + batch : nrec;
+        k_member_tuples<<<blocks_for(N), TPB, 0, s>>>(N, perm, c->labels, flag, rrank, r0, r1, c->row_ptr, tc);
+        note_launch();
+        SIVF_CUDA_TRY(scan_exclusive_i64(tc, toff, N, tot_d, ws, s));
+        int64_t T = 0;
+        SIVF_CUDA_TRY(cudaMemcpyAsync(&T, tot_d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        SIVF_CUDA_TRY(cudaStreamSynchronize(s));
+        moved_nnz += T;
+        if (T == 0) continue;
+        size_t mark = ws.used;
+        uint32_t *tk0 = ws.take<uint32_t>(T), *tv0 = ws.take<uint32_t>(T);
+        uint32_t *tk1 = ws.take<uint32_t>(T), *tv1 = ws.take<uint32_t>(T);
+        int64_t *head = ws.take<int64_t>(T), *uidx = ws.take<int64_t>(T);
+        if (!tk0 || !tv0 || !tk1 || !tv1 || !head || !uidx) return cudaErrorMemoryAllocation;
+        k_expand<<<blocks_for(N * 32), TPB, 0, s>>>(N, perm, c->labels, rrank, r0, tc, toff, c->row_ptr, c->idx,
+                                                     c->val, c->bits_t, tk0, tv0);
+        note_launch();
+        const int nbits = bits_for((uint64_t)(r1 - r0 - 1)) + c->bits_t;
+        bool a2 = false;
+        SIVF_CUDA_TRY(radix_sort_pairs(tk0, tv0, tk1, tv1, T, nbits, &a2, ws, s));
+        const uint32_t *sk = a2 ? tk1 : tk0, *sv = a2 ? tv1 : tv0;
+        k_heads<<<blocks_for(T), TPB, 0, s>>>(T, sk, head);
+        note_launch();
+        SIVF_CUDA_TRY(scan_exclusive_i64(head, uidx, T, tot_d, ws, s));
+        k_segsum<<<blocks_for(T), TPB, 0, s>>>(T, sk, sv, uidx, ubase, c->bits_t, r0, uterm, usum, sup);
+        note_launch();
+        SIVF_CUDA_TRY(cudaGetLastError());
+        int64_t U = 0;
+        SIVF_CUDA_TRY(cudaMemcpyAsync(&U, tot_d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        SIVF_CUDA_TRY(cudaStreamSynchronize(s));
+        ubase += U;
+        ws.used = mark;
+    }
+    SIVF_CUDA_TRY(scan_exclusive_i64(sup, supoff, nrec, nullptr, ws, s));
+
+    // u3/u4: new cluster-major rows
+    k_new_sizes<<<blocks_for(k), TPB, 0, s>>>(k, flag, rrank, sup, c->coff[old], sz);
+    note_launch();
+    SIVF_CUDA_TRY(scan_exclusive_i64(sz, c->coff[nw], k, tot_d, ws, s));
+    SIVF_CUDA_TRY(cudaMemcpyAsync(c->coff[nw] + k, tot_d, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    int64_t newn = 0;
+    SIVF_CUDA_TRY(cudaMemcpyAsync(&newn, tot_d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SIVF_CUDA_TRY(cudaStreamSynchronize(s));
+    if (newn > c->cap_c || newn >= 0x7FFFFFFFll) return cudaErrorMemoryAllocation;
+    k_write_rows<<<blocks_for((int64_t)k * 32), TPB, 0, s>>>(
+        k, flag, rrank, supoff, sup, uterm, usum, cnt, c->coff[old], c->cterm[old], c->cval[old], c->snorm,
+        c->coff[nw], c->cterm[nw], c->cval[nw], c->cclu, c->snorm_new, jAd, jUd);
+    note_launch();
+    k_sum2<<<1, 1024, 0, s>>>(k, jAd, jUd, c->obj_dev);
+    note_launch();
+    SIVF_CUDA_TRY(cudaGetLastError());
+    c->cur = nw;
+    c->c_nnz = newn;
+    double *t = c->snorm;
+    c->snorm = c->snorm_new;
+    c->snorm_new = t;
+    c->stats.moved_nnz = moved_nnz;
+    ws.reset();
+
+    // u5: rebuild the structured inverted file with lambda^[r]
+    SIVF_CUDA_TRY(build_inverted_file(c));
+    ws.reset();
+    return cudaSuccess;
+}
+
+}  // namespace sivf

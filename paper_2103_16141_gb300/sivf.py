@@ -1,0 +1,279 @@
+"""Python binding of libsivf.so (include/sivf.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library. PyTorch supplies device
+memory and the stream. There is no CPU fallback: loading fails loudly when the
+library is missing or cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+SIVF_OK, SIVF_ERR_INVALID_ARG, SIVF_ERR_BAD_CSR, SIVF_ERR_OOM, SIVF_ERR_CUDA, SIVF_ERR_TIMEOUT, SIVF_ERR_STATE = range(7)
+STATUS_NAMES = ["SIVF_OK", "SIVF_ERR_INVALID_ARG", "SIVF_ERR_BAD_CSR", "SIVF_ERR_OOM", "SIVF_ERR_CUDA",
+                "SIVF_ERR_TIMEOUT", "SIVF_ERR_STATE"]
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
+
+
+class sivf_config(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("icp", ctypes.c_int), ("threads", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int), ("mem_cap_bytes", ctypes.c_int64)]
+
+
+class sivf_stats(ctypes.Structure):
+    _fields_ = [("iter", ctypes.c_int32), ("changed", ctypes.c_int64), ("n_moving", ctypes.c_int64),
+                ("n_moving_prev", ctypes.c_int64), ("filtered", ctypes.c_int64), ("simcalc", ctypes.c_int64),
+                ("postings", ctypes.c_int64), ("rescored", ctypes.c_int64), ("rescore_cands", ctypes.c_int64),
+                ("centroid_nnz", ctypes.c_int64), ("moved_nnz", ctypes.c_int64),
+                ("objective_assign", ctypes.c_double), ("objective_update", ctypes.c_double),
+                ("ms_assign", ctypes.c_double), ("ms_update", ctypes.c_double), ("launches", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class SivfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libsivf.so (building it with nvcc if absent). Raises if it cannot."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"SIVF CUDA library not found at {path}; build it with __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        p, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        st = ctypes.c_int
+        lib.sivf_init.argtypes = [ctypes.POINTER(p), ctypes.POINTER(sivf_config), i64, i32, i32, p, p, p, p, p]
+        lib.sivf_init.restype = st
+        lib.sivf_reseed.argtypes = [p, p]
+        lib.sivf_reseed.restype = st
+        lib.sivf_assign.argtypes = [p, ctypes.POINTER(i64)]
+        lib.sivf_assign.restype = st
+        lib.sivf_update.argtypes = [p]
+        lib.sivf_update.restype = st
+        lib.sivf_run.argtypes = [p, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
+        lib.sivf_run.restype = st
+        lib.sivf_get_labels.argtypes = [p, p, ctypes.c_int]
+        lib.sivf_get_labels.restype = st
+        lib.sivf_set_labels.argtypes = [p, p, ctypes.c_int]
+        lib.sivf_set_labels.restype = st
+        lib.sivf_get_centroids.argtypes = [p, p, p, p, i64, ctypes.POINTER(i64)]
+        lib.sivf_get_centroids.restype = st
+        lib.sivf_get_inverted_file.argtypes = [p, p, p, p, p, i64, ctypes.POINTER(i64)]
+        lib.sivf_get_inverted_file.restype = st
+        lib.sivf_get_lambda.argtypes = [p, p]
+        lib.sivf_get_lambda.restype = st
+        lib.sivf_get_stats.argtypes = [p, ctypes.POINTER(sivf_stats)]
+        lib.sivf_get_stats.restype = st
+        lib.sivf_last_error.argtypes = [p]
+        lib.sivf_last_error.restype = ctypes.c_char_p
+        lib.sivf_destroy.argtypes = [p]
+        lib.sivf_destroy.restype = None
+        _lib = lib
+        return lib
+
+
+def _check(lib, ctx, status: int):
+    if status != SIVF_OK:
+        msg = lib.sivf_last_error(ctx) if ctx else b""
+        raise SivfError(status, (msg or b"").decode(errors="replace"))
+
+
+# ---- thin wrappers with the C names (pointers are ints) ----
+
+def sivf_init(cfg: sivf_config, N: int, D: int, k: int, row_ptr: int, idx: int, val: int, init_ids: int,
+              stream: int) -> int:
+    lib = load()
+    ctx = ctypes.c_void_p()
+    st = lib.sivf_init(ctypes.byref(ctx), ctypes.byref(cfg), N, D, k, row_ptr, idx, val, init_ids, stream)
+    _check(lib, None, st)
+    return ctx.value
+
+
+def sivf_reseed(ctx: int, init_ids: int) -> None:
+    lib = load()
+    _check(lib, ctx, lib.sivf_reseed(ctx, init_ids))
+
+
+def sivf_assign(ctx: int) -> int:
+    lib = load()
+    n = ctypes.c_int64(0)
+    _check(lib, ctx, lib.sivf_assign(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def sivf_update(ctx: int) -> None:
+    lib = load()
+    _check(lib, ctx, lib.sivf_update(ctx))
+
+
+def sivf_run(ctx: int, max_iter: int):
+    lib = load()
+    it = ctypes.c_int32(0)
+    obj = ctypes.c_double(0.0)
+    _check(lib, ctx, lib.sivf_run(ctx, max_iter, ctypes.byref(it), ctypes.byref(obj)))
+    return it.value, obj.value
+
+
+def sivf_get_labels(ctx: int, dst: int, dst_is_device: bool) -> None:
+    lib = load()
+    _check(lib, ctx, lib.sivf_get_labels(ctx, dst, int(dst_is_device)))
+
+
+def sivf_set_labels(ctx: int, src: int, src_is_device: bool) -> None:
+    lib = load()
+    _check(lib, ctx, lib.sivf_set_labels(ctx, src, int(src_is_device)))
+
+
+def sivf_get_stats(ctx: int) -> sivf_stats:
+    lib = load()
+    s = sivf_stats()
+    _check(lib, ctx, lib.sivf_get_stats(ctx, ctypes.byref(s)))
+    return s
+
+
+def sivf_destroy(ctx: int) -> None:
+    if ctx:
+        load().sivf_destroy(ctx)
+
+
+class SIVF:
+    """One clustering instance on the current CUDA device.
+
+    row_ptr / idx / val are torch tensors (int64 / int32 / float32) on the
+    device, or numpy arrays that are copied to the device. The object keeps
+    references to the device tensors for as long as the context lives, as the
+    library borrows them.
+    """
+
+    def __init__(self, row_ptr, idx, val, D: int, k: int, init_ids, precision: str = "fp32", icp: bool = True,
+                 threads: int = 0, ctas_per_sm: int = 0, mem_cap_bytes: int = 0, stream=None):
+        import numpy as np
+        import torch
+
+        dev = torch.device("cuda", torch.cuda.current_device())
+
+        def to_dev(a, dtype):
+            if isinstance(a, torch.Tensor):
+                return a.to(device=dev, dtype=dtype).contiguous()
+            return torch.from_numpy(np.ascontiguousarray(a)).to(device=dev, dtype=dtype)
+
+        self.row_ptr = to_dev(row_ptr, torch.int64)
+        self.idx = to_dev(idx, torch.int32)
+        self.val = to_dev(val, torch.float32)
+        self.N = int(self.row_ptr.numel() - 1)
+        self.D, self.k = int(D), int(k)
+        ini = np.ascontiguousarray(np.asarray(init_ids, dtype=np.int32))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        cfg = sivf_config(PRECISIONS[precision], int(bool(icp)), int(threads), int(ctas_per_sm), int(mem_cap_bytes))
+        self.ctx = sivf_init(cfg, self.N, self.D, self.k, self.row_ptr.data_ptr(), self.idx.data_ptr(),
+                             self.val.data_ptr(), ini.ctypes.data, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            sivf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reseed(self, init_ids) -> None:
+        import numpy as np
+        ini = np.ascontiguousarray(np.asarray(init_ids, dtype=np.int32))
+        sivf_reseed(self.ctx, ini.ctypes.data)
+
+    def assign(self) -> int:
+        return sivf_assign(self.ctx)
+
+    def update(self) -> None:
+        sivf_update(self.ctx)
+
+    def run(self, max_iter: int):
+        return sivf_run(self.ctx, max_iter)
+
+    def stats(self) -> dict:
+        return sivf_get_stats(self.ctx).as_dict()
+
+    def labels(self):
+        import numpy as np
+        out = np.empty(self.N, dtype=np.int32)
+        sivf_get_labels(self.ctx, out.ctypes.data, False)
+        return out
+
+    def labels_device(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.N, dtype=torch.int32, device=self.row_ptr.device)
+        sivf_get_labels(self.ctx, out.data_ptr(), True)
+        return out
+
+    def set_labels(self, labels) -> None:
+        import numpy as np
+        import torch
+        if isinstance(labels, torch.Tensor) and labels.is_cuda:
+            t = labels.to(torch.int32).contiguous()
+            sivf_set_labels(self.ctx, t.data_ptr(), True)
+        else:
+            a = np.ascontiguousarray(np.asarray(labels, dtype=np.int32))
+            sivf_set_labels(self.ctx, a.ctypes.data, False)
+
+    def lam(self):
+        import numpy as np
+        lib = load()
+        out = np.empty(self.k, dtype=np.uint8)
+        _check(lib, self.ctx, lib.sivf_get_lambda(self.ctx, out.ctypes.data))
+        return out
+
+    def centroids(self):
+        """(off[k+1], term[nnz], u[nnz] fp32), cluster-major master copy."""
+        import numpy as np
+        lib = load()
+        off = np.empty(self.k + 1, dtype=np.int64)
+        n = ctypes.c_int64(0)
+        st = lib.sivf_get_centroids(self.ctx, off.ctypes.data, None, None, 0, ctypes.byref(n))
+        if st not in (SIVF_OK, SIVF_ERR_INVALID_ARG):
+            _check(lib, self.ctx, st)
+        term = np.empty(max(n.value, 1), dtype=np.int32)
+        u = np.empty(max(n.value, 1), dtype=np.float32)
+        _check(lib, self.ctx, lib.sivf_get_centroids(self.ctx, off.ctypes.data, term.ctypes.data, u.ctypes.data,
+                                                     len(term), ctypes.byref(n)))
+        return off, term[:n.value], u[:n.value]
+
+    def inverted_file(self):
+        """(off[D+1], mf0[D], cid[nnz], u[nnz] fp32) of the structured inverted file."""
+        import numpy as np
+        lib = load()
+        off = np.empty(self.D + 1, dtype=np.int64)
+        mf0 = np.empty(self.D, dtype=np.int32)
+        n = ctypes.c_int64(0)
+        st = lib.sivf_get_inverted_file(self.ctx, off.ctypes.data, mf0.ctypes.data, None, None, 0, ctypes.byref(n))
+        if st not in (SIVF_OK, SIVF_ERR_INVALID_ARG):
+            _check(lib, self.ctx, st)
+        cid = np.empty(max(n.value, 1), dtype=np.int32)
+        u = np.empty(max(n.value, 1), dtype=np.float32)
+        _check(lib, self.ctx, lib.sivf_get_inverted_file(self.ctx, off.ctypes.data, mf0.ctypes.data,
+                                                         cid.ctypes.data, u.ctypes.data, len(cid), ctypes.byref(n)))
+        return off, mf0, cid[:n.value], u[:n.value]

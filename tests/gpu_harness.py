@@ -1,0 +1,90 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C ABI
+and compare with the FP64 oracle on the same seeded inputs."""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import Oracle
+from synth import generate, init_ids
+
+MARGIN_TIE = 1e-6      # labels may differ only where the FP64 top-2 margin is below this
+CENTROID_RTOL = 1e-5   # |u_gpu - u_oracle| <= 1e-5 |u_oracle| per posting
+OBJECTIVE_RTOL = 1e-6  # objectives within 1e-6 relative
+
+
+def corpus_for(w, seed=None):
+    c = generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, w.seed if seed is None else seed)
+    ini = init_ids(w.N, w.k, w.init_seed if seed is None else seed * 7 + 3)
+    return c, ini
+
+
+def gpu_instance(c, k, ini, precision="fp32", icp=True, **kw):
+    from paper_2103_16141_gb300 import SIVF
+    return SIVF(c.row_ptr, c.idx, c.val, c.D, k, ini, precision=precision, icp=icp, **kw)
+
+
+def compare_labels(gpu_lab, or_lab, best, second, what=""):
+    """Bit-exact labels except objects whose FP64 top-2 margin is < 1e-6.
+    Returns the number of tolerated near-tie mismatches."""
+    diff = np.nonzero(gpu_lab != or_lab)[0]
+    if len(diff):
+        margin = best[diff] - second[diff]
+        bad = diff[margin >= MARGIN_TIE]
+        assert len(bad) == 0, f"{what}: {len(bad)} label mismatches with margin >= 1e-6 (first {bad[:5]})"
+    return len(diff)
+
+
+def compare_centroids(sivf, orc):
+    off_g, term_g, u_g = sivf.centroids()
+    off_o, term_o, u_o, _ = orc.centroids()
+    assert np.array_equal(off_g, off_o), "centroid row sizes differ"
+    assert np.array_equal(term_g, term_o), "centroid sparsity patterns differ"
+    np.testing.assert_allclose(u_g.astype(np.float64), u_o, rtol=CENTROID_RTOL, atol=0)
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+def lockstep(c, k, ini, iters, precision="fp32", icp=True, check_centroids=True, check_counts=True, **kw):
+    """Both sides assign from identical state; the oracle's labels are pushed
+    into the GPU context (a no-op unless a near-tie differed), then both
+    update. Returns per-iteration records."""
+    g = gpu_instance(c, k, ini, precision=precision, icp=icp, **kw)
+    o = Oracle(c, k, ini, icp=icp)           # same mode: counts comparable
+    ou = Oracle(c, k, ini, icp=False)        # unfiltered twin: full top-2 margins
+    recs = []
+    try:
+        for _ in range(iters):
+            g.assign()
+            a = o.assign()
+            ou.assign()
+            st = g.stats()
+            lab_g, lab_o = g.labels(), o.labels()
+            assert np.array_equal(lab_o, ou.labels()), "oracle ICP invariant broken"
+            best, second, _ = ou.scores()
+            n_tie = compare_labels(lab_g, lab_o, best, second, f"iteration {a.r}")
+            if n_tie == 0 and check_counts:
+                assert st["changed"] == a.changed
+                assert st["n_moving"] == a.n_moving
+                assert np.array_equal(g.lam(), o.lam())
+                if icp:
+                    assert st["filtered"] == a.filtered
+                    assert st["simcalc"] == a.simcalc
+                    assert st["postings"] == a.postings
+            if n_tie:
+                g.set_labels(lab_o)
+            recs.append(dict(r=a.r, changed=a.changed, ties=n_tie, stats=st, oracle=a))
+            if a.r > 1 and a.changed == 0:
+                break
+            g.update()
+            u = o.update()
+            ou.update()
+            st = g.stats()
+            assert rel(st["objective_update"], u.objective) <= OBJECTIVE_RTOL
+            assert rel(st["objective_assign"], a.objective) <= OBJECTIVE_RTOL
+            if check_centroids:
+                compare_centroids(g, o)
+        return recs
+    finally:
+        g.close()

@@ -1,0 +1,55 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads without
+a GPU, and exports every function declared in include/sivf.h."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from paper_2103_16141_gb300 import _build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "sivf.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(sivf_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["sivf_init", "sivf_assign", "sivf_update", "sivf_run", "sivf_get_labels", "sivf_set_labels",
+                     "sivf_get_centroids", "sivf_get_stats", "sivf_last_error", "sivf_destroy"]:
+        assert required in names
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_null_context_is_rejected_without_a_gpu():
+    lib = ctypes.CDLL(_build.build())
+    lib.sivf_assign.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.sivf_update.argtypes = [ctypes.c_void_p]
+    lib.sivf_last_error.argtypes = [ctypes.c_void_p]
+    lib.sivf_last_error.restype = ctypes.c_char_p
+    lib.sivf_destroy.argtypes = [ctypes.c_void_p]
+    assert lib.sivf_assign(None, None) == 1  # SIVF_ERR_INVALID_ARG
+    assert lib.sivf_update(None) == 1
+    assert lib.sivf_last_error(None)
+    lib.sivf_destroy(None)
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.dirname(_build.__file__)
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(root, f)).read()
+                assert "oracle" not in re.findall(r"import\s+(\w+)", text)
+                assert "from oracle" not in text and "import oracle" not in text

@@ -1,0 +1,146 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Bar (labels): bit-exact at every iteration except objects whose FP64 top-2
+margin is below 1e-6 (counted). Centroids: same sparsity pattern, values
+within 1e-5 relative. Objectives: within 1e-6 relative.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from synth import CONFIGS
+from synth.corpus import from_dense
+from tests.gpu_harness import (compare_centroids, compare_labels, corpus_for, gpu_instance, lockstep, rel,
+                               OBJECTIVE_RTOL)
+from tests.helpers import random_dense_corpus
+
+pytestmark = pytest.mark.gpu
+
+
+def test_c1_lockstep_fp32_icp():
+    w = CONFIGS["c1"]
+    c, ini = corpus_for(w)
+    recs = lockstep(c, w.k, ini, w.max_iter)
+    assert recs[-1]["changed"] == 0 or len(recs) == w.max_iter
+
+
+@pytest.mark.parametrize("threads", [64, 128, 512])
+def test_mid_lockstep_block_sizes(threads):
+    # several tiles of objects, documents longer than one staging chunk, ragged tails
+    w = CONFIGS["c2"].scaled(N=6_000, D=8_000, k=60, hi=1500)
+    c, ini = corpus_for(w, seed=5)
+    lockstep(c, w.k, ini, 8, threads=threads)
+
+
+def test_free_running_c1_matches_oracle_every_iteration():
+    w = CONFIGS["c1"]
+    c, ini = corpus_for(w)
+    g = gpu_instance(c, w.k, ini)
+    o = Oracle(c, w.k, ini, icp=True)
+    ou = Oracle(c, w.k, ini, icp=False)
+    try:
+        for _ in range(w.max_iter):
+            g.assign()
+            a = o.assign()
+            ou.assign()
+            best, second, _ = ou.scores()
+            n = compare_labels(g.labels(), o.labels(), best, second, f"iteration {a.r}")
+            assert n == 0, "free-running trajectories diverged on a near-tie"
+            if a.r > 1 and a.changed == 0:
+                break
+            g.update()
+            u = o.update()
+            ou.update()
+            assert rel(g.stats()["objective_update"], u.objective) <= OBJECTIVE_RTOL
+    finally:
+        g.close()
+
+
+def test_icp_and_unfiltered_gpu_runs_are_bit_identical():
+    w = CONFIGS["c2"].scaled(N=8_000, D=10_000, k=80)
+    c, ini = corpus_for(w, seed=9)
+    f = gpu_instance(c, w.k, ini, icp=True)
+    u = gpu_instance(c, w.k, ini, icp=False)
+    try:
+        saw_filter = False
+        for _ in range(25):
+            nf, nu = f.assign(), u.assign()
+            assert nf == nu
+            assert np.array_equal(f.labels(), u.labels())
+            assert np.array_equal(f.lam(), u.lam())
+            sf, su = f.stats(), u.stats()
+            saw_filter |= sf["filtered"] > 0
+            assert su["simcalc"] == w.N * w.k
+            assert sf["postings"] <= su["postings"]
+            if sf["iter"] > 1 and nf == 0:
+                break
+            f.update()
+            u.update()
+            cf, cu = f.centroids(), u.centroids()
+            for x, y in zip(cf, cu):
+                assert np.array_equal(x, y)
+            assert f.stats()["objective_update"] == u.stats()["objective_update"]
+        assert saw_filter
+    finally:
+        f.close()
+        u.close()
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_mixed_precision_labels_match_oracle(precision):
+    w = CONFIGS["c2"].scaled(N=6_000, D=8_000, k=120)
+    c, ini = corpus_for(w, seed=13)
+    recs = lockstep(c, w.k, ini, 6, precision=precision)
+    assert sum(r["stats"]["rescored"] for r in recs) > 0
+
+
+def test_duplicate_documents_and_seed_ties():
+    # identical documents give identical seeds: exact ties broken by lowest index
+    X, c = random_dense_corpus(300, 200, 0.05, seed=3, dup_rows=40)
+    N = c.N
+    ini = np.array([0, N - 1, 5, 7, 11, 13, 17, 19], dtype=np.int32)  # rows 0 and N-1 are identical
+    lockstep(c, len(ini), ini, 15)
+
+
+def test_edge_cases_k1_kN_empty_rows():
+    X, c = random_dense_corpus(50, 300, 0.05, seed=4)
+    lockstep(c, 1, np.array([3], dtype=np.int32), 5)
+    lockstep(c, 50, np.random.default_rng(1).permutation(50).astype(np.int32), 5)
+    X = np.zeros((40, 30), dtype=np.float32)
+    rng = np.random.default_rng(2)
+    for i in range(36):
+        m = rng.random(30) < 0.2
+        m[rng.integers(30)] = True
+        X[i, m] = rng.random(m.sum()) + 0.1
+        X[i] /= np.linalg.norm(X[i])
+    X[36:, :] = 0.0  # four empty rows: every score is zero, label 0
+    lockstep(from_dense(X), 4, np.array([0, 1, 2, 3], dtype=np.int32), 10)
+
+
+def test_full_size_c2_sampled_against_oracle():
+    """The bench workload at full size (N = 300K, D = 100K, k = 1000), in the
+    bench's launch configuration: after each assignment a sample of objects is
+    scored one by one by the oracle against centroids rebuilt from the GPU's
+    own previous labels."""
+    w = CONFIGS["c2"]
+    c, ini = corpus_for(w)
+    g = gpu_instance(c, w.k, ini)
+    o = Oracle(c, w.k, ini, icp=False)
+    rng = np.random.default_rng(0)
+    try:
+        for r in range(1, 4):
+            g.assign()
+            lab = g.labels()
+            ids = np.sort(rng.choice(w.N, size=3000, replace=False))
+            lab_o, best, second = o.score_objects(ids)
+            compare_labels(lab[ids], lab_o, best, second, f"C2 iteration {r}")
+            o.set_labels(lab)
+            g.update()
+            u = o.update()
+            assert rel(g.stats()["objective_update"], u.objective) <= OBJECTIVE_RTOL
+        compare_centroids(g, o)
+    finally:
+        g.close()
