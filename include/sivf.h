@@ -185,6 +185,46 @@ const char *sivf_last_error(const sivf_ctx *ctx);
 /* sivf_destroy — free all library-owned device memory. Accepts NULL. */
 void sivf_destroy(sivf_ctx *ctx);
 
+/*
+ * Allocation-free inverted-file build. The paper has no counterpart: this
+ * entry point exists for callers that may not allocate device memory, such as
+ * an inference-engine plugin whose execution step must not allocate, or a
+ * service that reserves a fixed device-memory budget at start-up and cannot
+ * call cudaMalloc on a request path (the call can fail under that budget and
+ * it synchronises the device).
+ *
+ * sivf_build_inverted_file_noalloc — the structured inverted file that
+ * sivf_update builds: for every term, the centroids holding it, moving ones
+ * (lam[j] == 0) first and invariant ones (lam[j] == 1) after, ascending ids in
+ * each part, with their values. It allocates nothing: its scratch is a
+ * file-scope static device array of SIVF_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library holds until the process exits.
+ *   k, D      : clusters and terms; 1 <= D <= SIVF_NOALLOC_MAX_TERMS.
+ *   n_entries : HOST, total centroid non-zeros = coff[k];
+ *               0 <= n_entries <= SIVF_NOALLOC_MAX_ENTRIES.
+ *   coff      : DEVICE int64[k+1], cterm : DEVICE int32[n_entries] (ascending
+ *               terms in each row), cval : DEVICE float[n_entries] — the
+ *               cluster-major centroids (sivf_get_centroids layout).
+ *   lam       : DEVICE uint8[k], 1 = invariant.
+ *   if_off    : DEVICE int64[D+1] out, if_mf0 : DEVICE int32[D] out (front
+ *               length), if_cid : DEVICE int32[n_entries] out,
+ *               if_u : DEVICE float[n_entries] out. Caller-owned.
+ *   stream    : cudaStream_t; all work is ordered on it (nothing synchronises).
+ * Errors: SIVF_ERR_INVALID_ARG, with nothing launched, when a size is beyond
+ * the limits above or a pointer is NULL; SIVF_ERR_CUDA on a CUDA failure.
+ * The first call on a device looks up the scratch array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture begins. Every call reuses the same array and clears what
+ * must start at zero; calls that overlap on the GPU race on it.
+ */
+#define SIVF_NOALLOC_MAX_ENTRIES (1 << 20)
+#define SIVF_NOALLOC_MAX_TERMS (1 << 18)
+#define SIVF_NOALLOC_SCRATCH_BYTES (26u << 20)
+sivf_status sivf_build_inverted_file_noalloc(int32_t k, int32_t D, int64_t n_entries, const int64_t *coff,
+                                             const int32_t *cterm, const float *cval, const uint8_t *lam,
+                                             int64_t *if_off, int32_t *if_mf0, int32_t *if_cid, float *if_u,
+                                             void *stream);
+
 #ifdef __cplusplus
 }
 #endif

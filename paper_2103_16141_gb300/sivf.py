@@ -89,6 +89,8 @@ def load(build_if_missing: bool = True):
         lib.sivf_last_error.restype = ctypes.c_char_p
         lib.sivf_destroy.argtypes = [p]
         lib.sivf_destroy.restype = None
+        lib.sivf_build_inverted_file_noalloc.argtypes = [i32, i32, i64, p, p, p, p, p, p, p, p, p]
+        lib.sivf_build_inverted_file_noalloc.restype = st
         _lib = lib
         return lib
 
@@ -150,6 +152,15 @@ def sivf_get_stats(ctx: int) -> sivf_stats:
     s = sivf_stats()
     _check(lib, ctx, lib.sivf_get_stats(ctx, ctypes.byref(s)))
     return s
+
+
+def sivf_build_inverted_file_noalloc(k: int, D: int, n_entries: int, coff: int, cterm: int, cval: int, lam: int,
+                                     if_off: int, if_mf0: int, if_cid: int, if_u: int, stream: int) -> None:
+    """Allocation-free inverted-file build (device pointers as ints; see
+    include/sivf.h for who needs it and its size limits)."""
+    lib = load()
+    _check(lib, None, lib.sivf_build_inverted_file_noalloc(k, D, n_entries, coff, cterm, cval, lam, if_off, if_mf0,
+                                                           if_cid, if_u, stream))
 
 
 def sivf_destroy(ctx: int) -> None:
