@@ -160,9 +160,11 @@ sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t
     INIT_CUDA(dmalloc(c, &c->cclu, capc), "alloc");
     INIT_CUDA(dmalloc(c, &c->if_off, (size_t)D + 1), "alloc");
     INIT_CUDA(dmalloc(c, &c->if_mf0, D), "alloc");
-    INIT_CUDA(dmalloc(c, &c->if_cid, capc), "alloc");
-    INIT_CUDA(dmalloc(c, &c->if_val, capc), "alloc");
-    if (c->cfg.prec != SIVF_FP32) INIT_CUDA(dmalloc(c, &c->if_lp, capc), "alloc");
+    // the scan reads aligned groups of 4 postings: up to 3 entries past the
+    // last list, so the posting arrays carry a small tail pad
+    INIT_CUDA(dmalloc(c, &c->if_cid, capc + IF_PAD), "alloc");
+    INIT_CUDA(dmalloc(c, &c->if_val, capc + IF_PAD), "alloc");
+    if (c->cfg.prec != SIVF_FP32) INIT_CUDA(dmalloc(c, &c->if_lp, capc + IF_PAD), "alloc");
     INIT_CUDA(dmalloc(c, &c->ctr, 1), "alloc");
     INIT_CUDA(dmalloc(c, &c->obj_dev, 2), "alloc");
     INIT_CUDA(cudaMallocHost(reinterpret_cast<void **>(&c->ctr_host), sizeof(DevCounters)), "alloc host");

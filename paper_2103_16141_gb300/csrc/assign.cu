@@ -68,10 +68,10 @@ __device__ __forceinline__ float load_u(const void *p, int pos) {
     if (PREC == SIVF_FP32) {
         return __ldg(reinterpret_cast<const float *>(p) + pos);
     } else if (PREC == SIVF_BF16) {
-        unsigned short b = __ldg(reinterpret_cast<const unsigned short *>(p) + pos);
+        const unsigned short b = __ldg(reinterpret_cast<const unsigned short *>(p) + pos);
         return __uint_as_float(((unsigned)b) << 16);
     } else {
-        unsigned short b = __ldg(reinterpret_cast<const unsigned short *>(p) + pos);
+        const unsigned short b = __ldg(reinterpret_cast<const unsigned short *>(p) + pos);
         return __half2float(__ushort_as_half(b)) * FP16_INV_SCALE;
     }
 }
@@ -167,15 +167,18 @@ __device__ __forceinline__ int block_inclusive_scan_int(int x, int *warp_s, int 
     return warp_s[warp] + inc;
 }
 
+constexpr int CH = 128;  // postings per work item: 32 lanes x 4
+
 template <int T, int PREC>
 __global__ void __launch_bounds__(T) assign_kernel(AssignParams P) {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int NW = T / 32;
     const int kpad = (P.k + 3) & ~3;
     uint32_t *rho = smem;
-    float *s_v = reinterpret_cast<float *>(smem + kpad);
-    int *s_start = reinterpret_cast<int *>(s_v + T);
-    int *s_pre = s_start + T;
+    float *s_vs = reinterpret_cast<float *>(smem + kpad);
+    int *s_start = reinterpret_cast<int *>(s_vs + T);
+    int *s_len = s_start + T;
+    int *s_item = s_len + T;
     __shared__ int warp_i[32];
     __shared__ int s_total;
     __shared__ long long s_obj;
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(T) assign_kernel(AssignParams P) {
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int j = tid; j < kpad; j += T) rho[j] = 0u;
-    unsigned long long c_post = 0, c_filt = 0, c_sim = 0, c_resc = 0, c_cand = 0, c_chg = 0;
+    unsigned long long c_post_obj = 0, c_filt = 0, c_sim = 0, c_resc = 0, c_cand = 0, c_chg = 0;
     __syncthreads();
 
     for (;;) {
@@ -203,57 +206,66 @@ __global__ void __launch_bounds__(T) assign_kernel(AssignParams P) {
         const int n_mov = filt ? *P.n_mov : 0;
 
         // ---- similarity scan (Algorithm 4, lines 7-13) ----
+        // Work items are chunks of CH = 128 postings of one list (segment),
+        // aligned to 4 entries. A warp takes every NW-th item; lane l handles
+        // postings l, l+32, l+64, l+96 of the chunk (coalesced loads). Chunks
+        // wholly inside the segment take a mask-free path.
         for (int64_t cb = rb; cb < re; cb += T) {
             const int cn = (int)min((int64_t)T, re - cb);
-            int len = 0;
+            int nch = 0;
             if (tid < cn) {
                 const int t = P.idx[cb + tid];
                 const int64_t o0 = P.if_off[t];
-                len = filt ? P.if_mf0[t] : (int)(P.if_off[t + 1] - o0);
-                s_v[tid] = P.val[cb + tid];
+                const int len = filt ? P.if_mf0[t] : (int)(P.if_off[t + 1] - o0);
                 s_start[tid] = (int)o0;
+                s_len[tid] = len;
+                s_vs[tid] = P.val[cb + tid] * FIX_SCALE;  // exact: power-of-two scaling
+                nch = len > 0 ? (((int)o0 & 3) + len + CH - 1) / CH : 0;
+                c_post_obj += (unsigned long long)len;
             }
-            const int incl = block_inclusive_scan_int<T>(len, warp_i, &s_total);
-            s_pre[tid] = incl;
+            const int incl = block_inclusive_scan_int<T>(nch, warp_i, &s_total);
+            s_item[tid] = incl;
             __syncthreads();
-            const int L = s_total;
-            if (tid == 0) c_post += (unsigned long long)L;
-            int h = 0, beg = 0, end = s_pre[0], start = s_start[0];
-            float v = s_v[0];
-            for (int p0 = tid; p0 < L; p0 += 4 * T) {
-                int pos[4];
-                float vv[4];
+            const int items = s_total;
+            for (int it = warp; it < items; it += NW) {
+                int lo = 0, hi = cn - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_item[mid] > it) hi = mid; else lo = mid + 1;
+                }
+                const int h = lo;
+                const int c = it - (h ? s_item[h - 1] : 0);
+                const int sb = s_start[h], se = sb + s_len[h];
+                const float vs = s_vs[h];
+                const int a0 = (sb & ~3) + c * CH;
+                // lane-consecutive postings: a warp's 32 atomics per step hit
+                // consecutive ids on dense lists, i.e. distinct banks
+                if (a0 >= sb && a0 + CH <= se) {
+                    int cc[4];
+                    float uu[4];
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    const int p = p0 + m * T;
-                    pos[m] = -1;
-                    if (p < L) {
-                        while (p >= end) {
-                            ++h;
-                            beg = end;
-                            end = s_pre[h];
-                            start = s_start[h];
-                            v = s_v[h];
+                    for (int m = 0; m < 4; ++m) {
+                        cc[m] = __ldg(P.if_cid + a0 + 32 * m + lane);
+                        uu[m] = load_u<PREC>(P.if_vals, a0 + 32 * m + lane);
+                    }
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) atomicAdd(&rho[cc[m]], __float2uint_ru(vs * uu[m]));
+                } else {
+                    int cc[4];
+                    float uu[4];
+                    bool ok[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const int pos = a0 + 32 * m + lane;
+                        ok[m] = pos >= sb && pos < se;
+                        if (ok[m]) {
+                            cc[m] = __ldg(P.if_cid + pos);
+                            uu[m] = load_u<PREC>(P.if_vals, pos);
                         }
-                        pos[m] = start + (p - beg);
-                        vv[m] = v;
                     }
-                }
-                int cc[4];
-                float uu[4];
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    if (pos[m] >= 0) {
-                        cc[m] = __ldg(P.if_cid + pos[m]);
-                        uu[m] = load_u<PREC>(P.if_vals, pos[m]);
-                    }
-                }
-#pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    if (pos[m] >= 0) {
-                        const float prod = vv[m] * uu[m];
-                        atomicAdd(&rho[cc[m]], __float2uint_ru(prod * FIX_SCALE));
-                    }
+                    for (int m = 0; m < 4; ++m)
+                        if (ok[m]) atomicAdd(&rho[cc[m]], __float2uint_ru(vs * uu[m]));
                 }
             }
             __syncthreads();
@@ -376,8 +388,11 @@ __global__ void __launch_bounds__(T) assign_kernel(AssignParams P) {
         __syncthreads();
     }
 
+    // every thread staged a share of the terms: sum the posting counts
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c_post_obj += __shfl_xor_sync(0xffffffffu, c_post_obj, o);
+    if (lane == 0 && c_post_obj) atomicAdd(&P.ctr->postings, c_post_obj);
     if (tid == 0) {
-        atomicAdd(&P.ctr->postings, c_post);
         atomicAdd(&P.ctr->filtered, c_filt);
         atomicAdd(&P.ctr->simcalc, c_sim);
         atomicAdd(&P.ctr->changed, c_chg);
@@ -416,7 +431,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(int32_t k, int first_ite
 template <int T, int PREC>
 cudaError_t launch_t(sivf_ctx *c, const AssignParams &P, int ctas_per_sm) {
     const int kpad = (c->k + 3) & ~3;
-    const size_t smem = (size_t)kpad * 4 + (size_t)T * 12;
+    const size_t smem = (size_t)kpad * 4 + (size_t)T * 16;
     auto kern = assign_kernel<T, PREC>;
     SIVF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;

@@ -25,6 +25,8 @@
 namespace sivf {
 
 constexpr uint32_t OWN_INVALID = 0xFFFFFFFFu;
+// tail padding (entries) of the inverted-file posting arrays
+constexpr int64_t IF_PAD = 256;
 // Scores are accumulated as unsigned fixed point with quantum 2^-31:
 // q = ceil(fl(v * u) * 2^31). Cosine scores are <= 1 (+ rounding), so the
 // sum of an object's terms stays below 2^32.

@@ -174,24 +174,60 @@ __global__ void k_expand(int64_t N, const uint32_t *perm, const int32_t *labels,
     }
 }
 
-__global__ void k_heads(int64_t n, const uint32_t *keys, int64_t *head) {
+__global__ void k_heads(int64_t n, const uint32_t *keys, uint32_t *head) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        head[e] = (e == 0 || keys[e] != keys[e - 1]) ? 1 : 0;
+        head[e] = (e == 0 || keys[e] != keys[e - 1]) ? 1u : 0u;
 }
 
-// sequential FP64 sum of each run of equal keys, in input (ascending object) order
-__global__ void k_segsum(int64_t n, const uint32_t *keys, const uint32_t *vals, const int64_t *uidx, int64_t ubase,
-                         int bits_t, int64_t r0, int32_t *uterm, double *usum, int64_t *sup) {
+// position of each run of equal keys: hpos[u] = first element of run u
+__global__ void k_head_pos(int64_t n, const uint32_t *head, const uint32_t *uidx, uint32_t *hpos) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        if (head[e]) hpos[uidx[e]] = (uint32_t)e;
+}
+
+// FP64 sum of each run of equal keys (a (cluster, term) pair). Runs of up to
+// 32 elements are summed by one lane in input (ascending object) order; longer
+// runs by the whole warp: lane l takes elements l, l+32, ... in order, then a
+// butterfly reduction. Both orders are fixed, so the result is reproducible.
+__global__ void k_segsum(int64_t n, int64_t U, const uint32_t *keys, const uint32_t *vals, const uint32_t *hpos,
+                         int64_t ubase, int bits_t, int64_t r0, int32_t *uterm, double *usum, int64_t *sup) {
     const uint32_t tmask = (1u << bits_t) - 1u;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t key = keys[e];
-        if (e > 0 && keys[e - 1] == key) continue;
-        double s = 0.0;
-        for (int64_t f = e; f < n && keys[f] == key; ++f) s += (double)__uint_as_float(vals[f]);
-        const int64_t u = ubase + uidx[e];
-        uterm[u] = (int32_t)(key & tmask);
-        usum[u] = s;
-        atomicAdd(reinterpret_cast<unsigned long long *>(sup + r0 + (key >> bits_t)), 1ull);
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t ub = wid * 32; ub < U; ub += nw * 32) {
+        const int64_t u = ub + lane;
+        int64_t b = 0, e = 0;
+        bool longrun = false;
+        if (u < U) {
+            b = hpos[u];
+            e = (u + 1 < U) ? (int64_t)hpos[u + 1] : n;
+            longrun = (e - b) > 32;
+            if (!longrun) {
+                double acc = 0.0;
+                for (int64_t f = b; f < e; ++f) acc += (double)__uint_as_float(vals[f]);
+                const uint32_t key = keys[b];
+                uterm[ubase + u] = (int32_t)(key & tmask);
+                usum[ubase + u] = acc;
+                atomicAdd(reinterpret_cast<unsigned long long *>(sup + r0 + (key >> bits_t)), 1ull);
+            }
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, longrun);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t sb = __shfl_sync(0xffffffffu, b, src), se = __shfl_sync(0xffffffffu, e, src);
+            double acc = 0.0;
+            for (int64_t f = sb + lane; f < se; f += 32) acc += (double)__uint_as_float(vals[f]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) {
+                const uint32_t key = keys[sb];
+                uterm[ubase + ub + src] = (int32_t)(key & tmask);
+                usum[ubase + ub + src] = acc;
+                atomicAdd(reinterpret_cast<unsigned long long *>(sup + r0 + (key >> bits_t)), 1ull);
+            }
+        }
     }
 }
 
@@ -203,28 +239,42 @@ __global__ void k_new_sizes(int32_t k, const int64_t *flag, const int64_t *rrank
     if (j < k) sz[j] = flag[j] ? sup[rrank[j]] : coff_old[j + 1] - coff_old[j];
 }
 
-__global__ void k_write_rows(int32_t k, const int64_t *flag, const int64_t *rrank, const int64_t *supoff,
-                             const int64_t *sup, const int32_t *uterm, const double *usum, const int64_t *cnt,
-                             const int64_t *coff_old, const int32_t *cterm_old, const float *cval_old,
-                             const double *snorm_old, const int64_t *coff_new, int32_t *cterm_new, float *cval_new,
-                             int32_t *cclu_new, double *snorm_new, double *jA, double *jU) {
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (wid >= k) return;
-    const int j = (int)wid;
+// One CTA (WR_THREADS) per cluster. Recomputed clusters: ||s|| in FP64 with
+// strided per-thread sums and a fixed tree, u = s / ||s|| as FP32, and
+// <s_j, mu_j^[r-1]> by binary search of each term in the previous row.
+// Other clusters copy their previous row.
+constexpr int WR_THREADS = 256;
+
+__device__ __forceinline__ double block_sum_fixed(double x, double *sh) {
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int s = WR_THREADS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(WR_THREADS) k_write_rows(
+    int32_t k, const int64_t *flag, const int64_t *rrank, const int64_t *supoff, const int64_t *sup,
+    const int32_t *uterm, const double *usum, const int64_t *cnt, const int64_t *coff_old, const int32_t *cterm_old,
+    const float *cval_old, const double *snorm_old, const int64_t *coff_new, int32_t *cterm_new, float *cval_new,
+    int32_t *cclu_new, double *snorm_new, double *jA, double *jU) {
+    __shared__ double sh[WR_THREADS];
+    const int j = blockIdx.x;
+    if (j >= k) return;
     const int64_t o = coff_new[j];
+    const int64_t cb = coff_old[j], ce = coff_old[j + 1];
     if (flag[j]) {
         const int64_t r = rrank[j];
         const int64_t ub = supoff[r], n = sup[r];
         double ss = 0.0;
-        for (int64_t q = lane; q < n; q += 32) ss += usum[ub + q] * usum[ub + q];
-#pragma unroll
-        for (int s = 16; s > 0; s >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, s);
-        const double nrm = sqrt(ss);
-        // <s_j, mu_j^[r-1]>: binary search of each term in the previous row
-        const int64_t cb = coff_old[j], ce = coff_old[j + 1];
+        for (int64_t q = threadIdx.x; q < n; q += WR_THREADS) ss += usum[ub + q] * usum[ub + q];
+        const double nrm = sqrt(block_sum_fixed(ss, sh));
         double dot = 0.0;
-        for (int64_t q = lane; q < n; q += 32) {
+        for (int64_t q = threadIdx.x; q < n; q += WR_THREADS) {
             const int32_t t = uterm[ub + q];
             const double sv = usum[ub + q];
             cterm_new[o + q] = t;
@@ -232,26 +282,24 @@ __global__ void k_write_rows(int32_t k, const int64_t *flag, const int64_t *rran
             cclu_new[o + q] = j;
             int64_t lo = cb, hi = ce;
             while (lo < hi) {
-                int64_t mid = (lo + hi) >> 1;
+                const int64_t mid = (lo + hi) >> 1;
                 if (cterm_old[mid] < t) lo = mid + 1; else hi = mid;
             }
             if (lo < ce && cterm_old[lo] == t) dot += sv * (double)cval_old[lo];
         }
-#pragma unroll
-        for (int s = 16; s > 0; s >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, s);
-        if (lane == 0) {
+        dot = block_sum_fixed(dot, sh);
+        if (threadIdx.x == 0) {
             snorm_new[j] = nrm;
             jA[j] = dot;
             jU[j] = nrm;
         }
     } else {
-        const int64_t cb = coff_old[j], ce = coff_old[j + 1];
-        for (int64_t q = cb + lane; q < ce; q += 32) {
+        for (int64_t q = cb + threadIdx.x; q < ce; q += WR_THREADS) {
             cterm_new[o + (q - cb)] = cterm_old[q];
             cval_new[o + (q - cb)] = cval_old[q];
             cclu_new[o + (q - cb)] = j;
         }
-        if (lane == 0) {
+        if (threadIdx.x == 0) {
             const double sn = cnt[j] > 0 ? snorm_old[j] : 0.0;
             snorm_new[j] = sn;
             jA[j] = sn;  // unchanged members: <s_j, s_j / ||s_j||> = ||s_j||
@@ -491,8 +539,8 @@ cudaError_t run_update(sivf_ctx *c) {
         size_t mark = ws.used;
         uint32_t *tk0 = ws.take<uint32_t>(T), *tv0 = ws.take<uint32_t>(T);
         uint32_t *tk1 = ws.take<uint32_t>(T), *tv1 = ws.take<uint32_t>(T);
-        int64_t *head = ws.take<int64_t>(T), *uidx = ws.take<int64_t>(T);
-        if (!tk0 || !tv0 || !tk1 || !tv1 || !head || !uidx) return cudaErrorMemoryAllocation;
+        uint32_t *head = ws.take<uint32_t>(T), *uidx = ws.take<uint32_t>(T), *hpos = ws.take<uint32_t>(T);
+        if (!tk0 || !tv0 || !tk1 || !tv1 || !head || !uidx || !hpos) return cudaErrorMemoryAllocation;
         k_expand<<<blocks_for(N * 32), TPB, 0, s>>>(N, perm, c->labels, rrank, r0, tc, toff, c->row_ptr, c->idx,
                                                      c->val, c->bits_t, tk0, tv0);
         note_launch();
@@ -502,13 +550,19 @@ cudaError_t run_update(sivf_ctx *c) {
         const uint32_t *sk = a2 ? tk1 : tk0, *sv = a2 ? tv1 : tv0;
         k_heads<<<blocks_for(T), TPB, 0, s>>>(T, sk, head);
         note_launch();
-        SIVF_CUDA_TRY(scan_exclusive_i64(head, uidx, T, tot_d, ws, s));
-        k_segsum<<<blocks_for(T), TPB, 0, s>>>(T, sk, sv, uidx, ubase, c->bits_t, r0, uterm, usum, sup);
+        SIVF_CUDA_TRY(scan_exclusive_u32(head, uidx, T, ws, s));
+        // U = uidx[T-1] + head[T-1]
+        uint32_t tail[2] = {0, 0};
+        SIVF_CUDA_TRY(cudaMemcpyAsync(&tail[0], uidx + (T - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        SIVF_CUDA_TRY(cudaMemcpyAsync(&tail[1], head + (T - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        k_head_pos<<<blocks_for(T), TPB, 0, s>>>(T, head, uidx, hpos);
+        note_launch();
+        SIVF_CUDA_TRY(cudaStreamSynchronize(s));
+        const int64_t U = (int64_t)tail[0] + (int64_t)tail[1];
+        k_segsum<<<blocks_for((U + 31) / 32 * 32), TPB, 0, s>>>(T, U, sk, sv, hpos, ubase, c->bits_t, r0, uterm, usum,
+                                                                  sup);
         note_launch();
         SIVF_CUDA_TRY(cudaGetLastError());
-        int64_t U = 0;
-        SIVF_CUDA_TRY(cudaMemcpyAsync(&U, tot_d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        SIVF_CUDA_TRY(cudaStreamSynchronize(s));
         ubase += U;
         ws.used = mark;
     }
@@ -522,8 +576,8 @@ cudaError_t run_update(sivf_ctx *c) {
     int64_t newn = 0;
     SIVF_CUDA_TRY(cudaMemcpyAsync(&newn, tot_d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     SIVF_CUDA_TRY(cudaStreamSynchronize(s));
-    if (newn > c->cap_c || newn >= 0x7FFFFFFFll) return cudaErrorMemoryAllocation;
-    k_write_rows<<<blocks_for((int64_t)k * 32), TPB, 0, s>>>(
+    if (newn > c->cap_c || newn >= 0x7FFFFFFFll - 2 * IF_PAD) return cudaErrorMemoryAllocation;
+    k_write_rows<<<(unsigned)k, WR_THREADS, 0, s>>>(
         k, flag, rrank, supoff, sup, uterm, usum, cnt, c->coff[old], c->cterm[old], c->cval[old], c->snorm,
         c->coff[nw], c->cterm[nw], c->cval[nw], c->cclu, c->snorm_new, jAd, jUd);
     note_launch();
