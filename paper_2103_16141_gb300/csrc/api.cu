@@ -48,7 +48,7 @@ cudaError_t dmalloc(sivf_ctx *c, T **p, size_t n) {
 void free_all(sivf_ctx *c) {
     void *ptrs[] = {c->labels, c->labels_prev, c->own, c->sumv, c->lam, c->lam_prev, c->moving, c->mov_list,
                     c->n_mov_dev, c->snorm, c->snorm_new, c->coff[0], c->coff[1], c->cterm[0], c->cterm[1],
-                    c->cval[0], c->cval[1], c->cclu, c->if_off, c->if_mf0, c->if_cid, c->if_val, c->if_lp,
+                    c->cval[0], c->cval[1], c->cclu, c->if_off, c->if_mf0, c->if_cid, c->if_cid16, c->if_val, c->if_lp,
                     c->ctr, c->obj_dev, c->ws.base};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -65,7 +65,7 @@ sivf_status check_usable(sivf_ctx *c) {
 
 void pick_assign_config(sivf_ctx *c) {
     int T = c->cfg.threads;
-    if (T != 64 && T != 128 && T != 256 && T != 512 && T != 1024) T = 0;
+    if (T != 64 && T != 128 && T != 256 && T != 512) T = 0;
     if (T == 0) T = c->k <= 256 ? 64 : (c->k <= 4096 ? 128 : 512);
     c->assign_threads = T;
     c->assign_ctas_per_sm = c->cfg.ctas_per_sm > 0 ? c->cfg.ctas_per_sm : 0;
@@ -163,6 +163,7 @@ sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t
     // the scan reads aligned groups of 4 postings: up to 3 entries past the
     // last list, so the posting arrays carry a small tail pad
     INIT_CUDA(dmalloc(c, &c->if_cid, capc + IF_PAD), "alloc");
+    if (k <= 65536) INIT_CUDA(dmalloc(c, &c->if_cid16, capc + IF_PAD), "alloc");
     INIT_CUDA(dmalloc(c, &c->if_val, capc + IF_PAD), "alloc");
     if (c->cfg.prec != SIVF_FP32) INIT_CUDA(dmalloc(c, &c->if_lp, capc + IF_PAD), "alloc");
     INIT_CUDA(dmalloc(c, &c->ctr, 1), "alloc");
@@ -171,12 +172,15 @@ sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t
     {
         // workspace: max of the update's two phases, plus primitive scratch
         const size_t n8 = (size_t)N * 8, k8 = (size_t)k * 8;
-        size_t phase1 = 4 * (size_t)N * 4 + 2 * n8 + 10 * k8 + 16 * ((size_t)nnz + 1) + 12 * ((size_t)nnz + 1) +
-                        16 * ((size_t)nnz + 1) + 16 * 4096;
+        // u1: 4 label key/value arrays (4 B x N), tuple counts/offsets (8 B x N),
+        // per-cluster arrays; u2: unique (term, sum) pairs (12 B x nnz) and
+        // per tuple 4 sort arrays, head/index/position and a piece sum (36 B)
+        size_t phase1 = 4 * (size_t)N * 4 + 2 * n8 + 10 * k8 + 12 * ((size_t)nnz + 1) + 36 * ((size_t)nnz + 1) +
+                        32 * 4096;
         size_t phase2 = 16 * ((size_t)capc + 1) + 24 * ((size_t)D + 1) + 16 * 4096;
         size_t ws = phase1 > phase2 ? phase1 : phase2;
         size_t maxn = (size_t)(capc > N ? capc : N);
-        ws += (maxn / 4096 + 2) * 256 * 4 + (maxn / 2048 + 2) * 16 + 64 * 256 + (1 << 20);
+        ws += (maxn / 4096 + 2) * 1024 * 4 + (maxn / 2048 + 2) * 16 + 64 * 256 + (1 << 20);
         c->ws_bytes = ws;
         INIT_CUDA(dmalloc(c, reinterpret_cast<char **>(&c->ws.base), ws), "alloc workspace");
         c->ws.cap = ws;

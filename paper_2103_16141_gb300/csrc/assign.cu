@@ -48,6 +48,7 @@ struct AssignParams {
     const int64_t *if_off;
     const int32_t *if_mf0;
     const int32_t *if_cid;
+    const uint16_t *if_cid16;
     const void *if_vals;
     const int64_t *coff;
     const int32_t *cterm;
@@ -167,10 +168,40 @@ __device__ __forceinline__ int block_inclusive_scan_int(int x, int *warp_s, int 
     return warp_s[warp] + inc;
 }
 
-constexpr int CH = 128;  // postings per work item: 32 lanes x 4
+constexpr int UNR = 8;         // postings per lane per work item
+constexpr int CH = 32 * UNR;   // postings per work item
 
-template <int T, int PREC>
-__global__ void __launch_bounds__(T) assign_kernel(AssignParams P) {
+// Typed base pointers of the posting arrays and value decoding.
+template <bool CID16>
+__device__ __forceinline__ auto cid_base(const AssignParams &P) {
+    if constexpr (CID16) return P.if_cid16;
+    else return P.if_cid;
+}
+
+template <int PREC>
+__device__ __forceinline__ auto val_base(const void *p) {
+    if constexpr (PREC == SIVF_FP32) return reinterpret_cast<const float *>(p);
+    else return reinterpret_cast<const unsigned short *>(p);
+}
+
+template <int PREC>
+__device__ __forceinline__ float decode_u(float x) { return x; }
+template <int PREC>
+__device__ __forceinline__ float decode_u(unsigned short b) {
+    if constexpr (PREC == SIVF_BF16) return __uint_as_float(((unsigned)b) << 16);
+    else return __half2float(__ushort_as_half(b)) * FP16_INV_SCALE;
+}
+
+// Register budget: resident CTAs per SM at 128 threads (scaled for other
+// block sizes). 10 caps a thread at 51 registers (measured best on the
+// 300K x 100K, k = 1000 corpus among 8, 10, 12 and 16).
+#ifndef SIVF_ASSIGN_MIN_CTAS_128
+#define SIVF_ASSIGN_MIN_CTAS_128 10
+#endif
+
+template <int T, int PREC, bool CID16>
+__global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) : 1)
+    assign_kernel(AssignParams P) {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int NW = T / 32;
     const int kpad = (P.k + 3) & ~3;
@@ -206,10 +237,12 @@ __global__ void __launch_bounds__(T) assign_kernel(AssignParams P) {
         const int n_mov = filt ? *P.n_mov : 0;
 
         // ---- similarity scan (Algorithm 4, lines 7-13) ----
-        // Work items are chunks of CH = 128 postings of one list (segment),
-        // aligned to 4 entries. A warp takes every NW-th item; lane l handles
-        // postings l, l+32, l+64, l+96 of the chunk (coalesced loads). Chunks
-        // wholly inside the segment take a mask-free path.
+        // Work items are chunks of CH = 32 * UNR postings of one list
+        // (segment), aligned to 4 entries. A warp takes every NW-th item; lane
+        // l handles postings l, l+32, ... of the chunk (coalesced loads, and on
+        // dense lists the 32 atomics of one step hit consecutive ids, i.e.
+        // distinct banks). Chunks wholly inside the segment take a mask-free
+        // path.
         for (int64_t cb = rb; cb < re; cb += T) {
             const int cn = (int)min((int64_t)T, re - cb);
             int nch = 0;
@@ -227,44 +260,43 @@ __global__ void __launch_bounds__(T) assign_kernel(AssignParams P) {
             s_item[tid] = incl;
             __syncthreads();
             const int items = s_total;
+            // items are visited in increasing order, so the owning term index
+            // only moves forward
+            int h = 0;
             for (int it = warp; it < items; it += NW) {
-                int lo = 0, hi = cn - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (s_item[mid] > it) hi = mid; else lo = mid + 1;
-                }
-                const int h = lo;
+                while (s_item[h] <= it) ++h;
                 const int c = it - (h ? s_item[h - 1] : 0);
                 const int sb = s_start[h], se = sb + s_len[h];
                 const float vs = s_vs[h];
                 const int a0 = (sb & ~3) + c * CH;
-                // lane-consecutive postings: a warp's 32 atomics per step hit
-                // consecutive ids on dense lists, i.e. distinct banks
+                // one base address per item; the UNR loads use immediate offsets
+                const auto *pc = cid_base<CID16>(P) + (a0 + lane);
+                const auto *pv = val_base<PREC>(P.if_vals) + (a0 + lane);
                 if (a0 >= sb && a0 + CH <= se) {
-                    int cc[4];
-                    float uu[4];
+                    int cc[UNR];
+                    float uu[UNR];
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        cc[m] = __ldg(P.if_cid + a0 + 32 * m + lane);
-                        uu[m] = load_u<PREC>(P.if_vals, a0 + 32 * m + lane);
+                    for (int m = 0; m < UNR; ++m) {
+                        cc[m] = (int)__ldg(pc + 32 * m);
+                        uu[m] = decode_u<PREC>(__ldg(pv + 32 * m));
                     }
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) atomicAdd(&rho[cc[m]], __float2uint_ru(vs * uu[m]));
+                    for (int m = 0; m < UNR; ++m) atomicAdd(&rho[cc[m]], __float2uint_ru(vs * uu[m]));
                 } else {
-                    int cc[4];
-                    float uu[4];
-                    bool ok[4];
+                    int cc[UNR];
+                    float uu[UNR];
+                    bool ok[UNR];
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
+                    for (int m = 0; m < UNR; ++m) {
                         const int pos = a0 + 32 * m + lane;
                         ok[m] = pos >= sb && pos < se;
                         if (ok[m]) {
-                            cc[m] = __ldg(P.if_cid + pos);
-                            uu[m] = load_u<PREC>(P.if_vals, pos);
+                            cc[m] = (int)__ldg(pc + 32 * m);
+                            uu[m] = decode_u<PREC>(__ldg(pv + 32 * m));
                         }
                     }
 #pragma unroll
-                    for (int m = 0; m < 4; ++m)
+                    for (int m = 0; m < UNR; ++m)
                         if (ok[m]) atomicAdd(&rho[cc[m]], __float2uint_ru(vs * uu[m]));
                 }
             }
@@ -428,11 +460,11 @@ __global__ void __launch_bounds__(1024) finalize_kernel(int32_t k, int first_ite
     }
 }
 
-template <int T, int PREC>
+template <int T, int PREC, bool CID16>
 cudaError_t launch_t(sivf_ctx *c, const AssignParams &P, int ctas_per_sm) {
     const int kpad = (c->k + 3) & ~3;
     const size_t smem = (size_t)kpad * 4 + (size_t)T * 16;
-    auto kern = assign_kernel<T, PREC>;
+    auto kern = assign_kernel<T, PREC, CID16>;
     SIVF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     SIVF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, smem));
@@ -444,17 +476,20 @@ cudaError_t launch_t(sivf_ctx *c, const AssignParams &P, int ctas_per_sm) {
     return cudaGetLastError();
 }
 
-template <int PREC>
+template <int PREC, bool CID16>
 cudaError_t launch_prec(sivf_ctx *c, const AssignParams &P) {
-    const int T = c->assign_threads;
     const int cps = c->assign_ctas_per_sm;
-    switch (T) {
-        case 64: return launch_t<64, PREC>(c, P, cps);
-        case 128: return launch_t<128, PREC>(c, P, cps);
-        case 256: return launch_t<256, PREC>(c, P, cps);
-        case 512: return launch_t<512, PREC>(c, P, cps);
-        default: return launch_t<1024, PREC>(c, P, cps);
+    switch (c->assign_threads) {
+        case 64: return launch_t<64, PREC, CID16>(c, P, cps);
+        case 128: return launch_t<128, PREC, CID16>(c, P, cps);
+        case 256: return launch_t<256, PREC, CID16>(c, P, cps);
+        default: return launch_t<512, PREC, CID16>(c, P, cps);
     }
+}
+
+template <int PREC>
+cudaError_t launch_ids(sivf_ctx *c, const AssignParams &P) {
+    return P.if_cid16 ? launch_prec<PREC, true>(c, P) : launch_prec<PREC, false>(c, P);
 }
 
 }  // namespace
@@ -471,6 +506,7 @@ cudaError_t launch_assign(sivf_ctx *c) {
     P.if_off = c->if_off;
     P.if_mf0 = c->if_mf0;
     P.if_cid = c->if_cid;
+    P.if_cid16 = c->if_cid16;
     P.if_vals = c->cfg.prec == SIVF_FP32 ? (const void *)c->if_val : (const void *)c->if_lp;
     P.coff = c->coff[c->cur];
     P.cterm = c->cterm[c->cur];
@@ -494,9 +530,9 @@ cudaError_t launch_assign(sivf_ctx *c) {
         P.eta = 0.0;
     }
     switch (c->cfg.prec) {
-        case SIVF_BF16: return launch_prec<SIVF_BF16>(c, P);
-        case SIVF_FP16: return launch_prec<SIVF_FP16>(c, P);
-        default: return launch_prec<SIVF_FP32>(c, P);
+        case SIVF_BF16: return launch_ids<SIVF_BF16>(c, P);
+        case SIVF_FP16: return launch_ids<SIVF_FP16>(c, P);
+        default: return launch_ids<SIVF_FP32>(c, P);
     }
 }
 

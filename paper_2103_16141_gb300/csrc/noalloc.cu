@@ -31,7 +31,7 @@ constexpr size_t kMaxTerms = SIVF_NOALLOC_MAX_TERMS;
 // scratch layout, taken by a bump allocator in this order (256-byte aligned):
 // cluster id, keys, values, keys', values' (4 B x entries each), per (term,
 // part) counts (2 x terms x 4 B), list lengths ((terms + 1) x 8 B), radix
-// histogram and scan partials (a few hundred KiB).
+// histogram (at most 1 MiB at the limits) and scan partials.
 constexpr size_t kScratchBytes = SIVF_NOALLOC_SCRATCH_BYTES;
 static_assert(kScratchBytes >= 5 * 4 * kMaxEntries + 2 * 4 * kMaxTerms + 8 * (kMaxTerms + 1) + (1u << 20),
               "scratch too small for the stated limits");

@@ -3,9 +3,10 @@
 //
 // Scan: reduce-then-scan in three launches (tile sums, one-CTA scan of the
 // tile sums, tile-local scan plus carry-in).
-// Radix sort: 8-bit digits, per pass (1) per-tile digit histograms stored
-// digit-major, (2) an exclusive scan of that table, (3) a stable scatter
-// whose in-tile ranks come from warp-level __match_any_sync on the digit.
+// Radix sort: digits of up to 10 bits (fewest passes for the key width), per
+// pass (1) per-tile digit histograms stored digit-major, (2) an exclusive
+// scan of that table, (3) a stable scatter whose in-tile ranks come from
+// warp-level __match_any_sync on the digit.
 #include "sivf_internal.cuh"
 
 namespace sivf {
@@ -125,13 +126,15 @@ constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 4096
-constexpr int RS_BITS = 8;
-constexpr int RS_RADIX = 1 << RS_BITS;
+constexpr int RS_MAX_BITS = 10;                 // digit width of one pass (<= 1024 buckets)
 
-__global__ void __launch_bounds__(RS_THREADS) radix_hist(const uint32_t *keys, int64_t n, int shift, uint32_t mask,
+template <int BITS>
+__global__ void __launch_bounds__(RS_THREADS) radix_hist(const uint32_t *keys, int64_t n, int shift,
                                                          uint32_t *counts, int64_t tiles) {
-    __shared__ uint32_t h[RS_RADIX];
-    for (int d = threadIdx.x; d < RS_RADIX; d += RS_THREADS) h[d] = 0;
+    constexpr int R = 1 << BITS;
+    constexpr uint32_t mask = R - 1;
+    __shared__ uint32_t h[R];
+    for (int d = threadIdx.x; d < R; d += RS_THREADS) h[d] = 0;
     __syncthreads();
     int64_t base = (int64_t)blockIdx.x * RS_TILE;
     for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
@@ -139,18 +142,21 @@ __global__ void __launch_bounds__(RS_THREADS) radix_hist(const uint32_t *keys, i
         if (p < n) atomicAdd(&h[(keys[p] >> shift) & mask], 1u);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < RS_RADIX; d += RS_THREADS) counts[(int64_t)d * tiles + blockIdx.x] = h[d];
+    for (int d = threadIdx.x; d < R; d += RS_THREADS) counts[(int64_t)d * tiles + blockIdx.x] = h[d];
 }
 
+template <int BITS>
 __global__ void __launch_bounds__(RS_THREADS) radix_scatter(const uint32_t *__restrict__ kin,
                                                             const uint32_t *__restrict__ vin,
                                                             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
-                                                            int64_t n, int shift, uint32_t mask,
+                                                            int64_t n, int shift,
                                                             const uint32_t *__restrict__ offs, int64_t tiles) {
-    __shared__ uint32_t wcnt[RS_WARPS][RS_RADIX];
-    __shared__ uint32_t toff[RS_RADIX];
+    constexpr int R = 1 << BITS;
+    constexpr uint32_t mask = R - 1;
+    __shared__ uint32_t wcnt[RS_WARPS][R];
+    __shared__ uint32_t toff[R];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < RS_RADIX; d += RS_THREADS) {
+    for (int d = threadIdx.x; d < R; d += RS_THREADS) {
 #pragma unroll
         for (int w = 0; w < RS_WARPS; ++w) wcnt[w][d] = 0;
         toff[d] = offs[(int64_t)d * tiles + blockIdx.x];
@@ -166,7 +172,7 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter(const uint32_t *__re
         uint32_t key = valid ? kin[p] : 0u;
         kk[r] = key;
         vv[r] = valid ? vin[p] : 0u;
-        uint32_t d = valid ? ((key >> shift) & mask) : (uint32_t)RS_RADIX;  // sentinel groups invalid lanes
+        uint32_t d = valid ? ((key >> shift) & mask) : (uint32_t)R;  // sentinel groups invalid lanes
         unsigned peers = __match_any_sync(0xffffffffu, d);
         uint32_t old = valid ? wcnt[warp][d] : 0u;
         __syncwarp();
@@ -175,7 +181,7 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter(const uint32_t *__re
         rk[r] = old + (uint32_t)__popc(peers & lt);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < RS_RADIX; d += RS_THREADS) {
+    for (int d = threadIdx.x; d < R; d += RS_THREADS) {
         uint32_t run = 0;
 #pragma unroll
         for (int w = 0; w < RS_WARPS; ++w) {
@@ -197,6 +203,19 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter(const uint32_t *__re
     }
 }
 
+template <int BITS>
+void radix_pass(const uint32_t *ka, const uint32_t *va, uint32_t *kb, uint32_t *vb, int64_t n, int shift,
+                uint32_t *counts, int64_t tiles, Workspace &ws, cudaStream_t s, cudaError_t *err) {
+    radix_hist<BITS><<<(unsigned)tiles, RS_THREADS, 0, s>>>(ka, n, shift, counts, tiles);
+    cudaError_t e = scan_exclusive_impl<uint32_t>(counts, counts, tiles * (1 << BITS), nullptr, ws, s);
+    if (e != cudaSuccess) {
+        *err = e;
+        return;
+    }
+    radix_scatter<BITS><<<(unsigned)tiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, counts, tiles);
+    note_launch(2);
+}
+
 }  // namespace
 
 cudaError_t scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total, Workspace &ws,
@@ -212,20 +231,30 @@ cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t 
                              bool *result_in_alt, Workspace &ws, cudaStream_t s) {
     *result_in_alt = false;
     if (n <= 1 || nbits <= 0) return cudaSuccess;
-    if (n > (int64_t)0xFFFFFFFFll) return cudaErrorInvalidValue;
+    if (n > (int64_t)0xFFFFFFFFll || nbits > 32) return cudaErrorInvalidValue;
+    // fewest passes of at most RS_MAX_BITS bits, widths as equal as possible
+    const int passes = (nbits + RS_MAX_BITS - 1) / RS_MAX_BITS;
+    const int width = (nbits + passes - 1) / passes;
     int64_t tiles = (n + RS_TILE - 1) / RS_TILE;
     size_t mark = ws.used;
-    uint32_t *counts = ws.take<uint32_t>((size_t)tiles * RS_RADIX);
+    uint32_t *counts = ws.take<uint32_t>((size_t)tiles << width);
     if (!counts) return cudaErrorMemoryAllocation;
     uint32_t *ka = k0, *va = v0, *kb = k1, *vb = v1;
-    for (int shift = 0; shift < nbits; shift += RS_BITS) {
-        int w = nbits - shift < RS_BITS ? nbits - shift : RS_BITS;
-        uint32_t mask = (1u << w) - 1u;
-        radix_hist<<<(unsigned)tiles, RS_THREADS, 0, s>>>(ka, n, shift, mask, counts, tiles);
-        cudaError_t e = scan_exclusive_impl<uint32_t>(counts, counts, tiles * RS_RADIX, nullptr, ws, s);
-        if (e != cudaSuccess) return e;
-        radix_scatter<<<(unsigned)tiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, mask, counts, tiles);
-        note_launch(2);
+    cudaError_t err = cudaSuccess;
+    for (int shift = 0; shift < nbits; shift += width) {
+        switch (width) {
+            case 1: radix_pass<1>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
+            case 2: radix_pass<2>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
+            case 3: radix_pass<3>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
+            case 4: radix_pass<4>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
+            case 5: radix_pass<5>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
+            case 6: radix_pass<6>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
+            case 7: radix_pass<7>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
+            case 8: radix_pass<8>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
+            case 9: radix_pass<9>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
+            default: radix_pass<10>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
+        }
+        if (err != cudaSuccess) return err;
         uint32_t *t = ka; ka = kb; kb = t;
         t = va; va = vb; vb = t;
         *result_in_alt = !*result_in_alt;

@@ -12,7 +12,8 @@
 //                                        cluster-major FP32 master copy, ascending terms
 //   snorm                 f64[k]        ||s_j|| of the sum behind each centroid
 //   inverted file         if_off int64[D+1], if_mf0 int32[D], if_cid int32[cap],
-//                                        if_val f32[cap], if_lp u16[cap] (bf16/fp16 copy)
+//                                        if_cid16 u16[cap] (k <= 65536), if_val f32[cap],
+//                                        if_lp u16[cap] (bf16/fp16 copy)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -108,6 +109,7 @@ struct sivf_ctx {
     int64_t *if_off = nullptr;
     int32_t *if_mf0 = nullptr;
     int32_t *if_cid = nullptr;
+    uint16_t *if_cid16 = nullptr;  // 16-bit copy of if_cid when k <= 65536 (read by the scan)
     float *if_val = nullptr;
     uint16_t *if_lp = nullptr;
     int64_t if_nnz = 0;

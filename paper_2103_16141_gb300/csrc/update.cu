@@ -185,49 +185,51 @@ __global__ void k_head_pos(int64_t n, const uint32_t *head, const uint32_t *uidx
         if (head[e]) hpos[uidx[e]] = (uint32_t)e;
 }
 
-// FP64 sum of each run of equal keys (a (cluster, term) pair). Runs of up to
-// 32 elements are summed by one lane in input (ascending object) order; longer
-// runs by the whole warp: lane l takes elements l, l+32, ... in order, then a
-// butterfly reduction. Both orders are fixed, so the result is reproducible.
-__global__ void k_segsum(int64_t n, int64_t U, const uint32_t *keys, const uint32_t *vals, const uint32_t *hpos,
-                         int64_t ubase, int bits_t, int64_t r0, int32_t *uterm, double *usum, int64_t *sup) {
-    const uint32_t tmask = (1u << bits_t) - 1u;
+// FP64 sum of each run of equal keys (a (cluster, term) pair), in two passes
+// with a fixed order (reproducible bit for bit):
+//  1. each warp takes 32 consecutive elements and forms, by a segmented
+//     inclusive scan over the lanes, the sum of every run piece inside those
+//     32 elements, stored at the piece's last element;
+//  2. one thread per run adds its pieces in ascending position.
+__global__ void k_seg_pieces(int64_t n, const uint32_t *keys, const uint32_t *vals, double *part) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t ub = wid * 32; ub < U; ub += nw * 32) {
-        const int64_t u = ub + lane;
-        int64_t b = 0, e = 0;
-        bool longrun = false;
-        if (u < U) {
-            b = hpos[u];
-            e = (u + 1 < U) ? (int64_t)hpos[u + 1] : n;
-            longrun = (e - b) > 32;
-            if (!longrun) {
-                double acc = 0.0;
-                for (int64_t f = b; f < e; ++f) acc += (double)__uint_as_float(vals[f]);
-                const uint32_t key = keys[b];
-                uterm[ubase + u] = (int32_t)(key & tmask);
-                usum[ubase + u] = acc;
-                atomicAdd(reinterpret_cast<unsigned long long *>(sup + r0 + (key >> bits_t)), 1ull);
-            }
-        }
-        unsigned todo = __ballot_sync(0xffffffffu, longrun);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int64_t sb = __shfl_sync(0xffffffffu, b, src), se = __shfl_sync(0xffffffffu, e, src);
-            double acc = 0.0;
-            for (int64_t f = sb + lane; f < se; f += 32) acc += (double)__uint_as_float(vals[f]);
+    for (int64_t base = wid * 32; base < n; base += nw * 32) {
+        const int64_t e = base + lane;
+        const bool valid = e < n;
+        const uint32_t key = valid ? keys[e] : 0xFFFFFFFFu;
+        double x = valid ? (double)__uint_as_float(vals[e]) : 0.0;
+        const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+        bool flag = lane == 0 || prev != key;  // a piece starts here
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) {
-                const uint32_t key = keys[sb];
-                uterm[ubase + ub + src] = (int32_t)(key & tmask);
-                usum[ubase + ub + src] = acc;
-                atomicAdd(reinterpret_cast<unsigned long long *>(sup + r0 + (key >> bits_t)), 1ull);
-            }
+        for (int o = 1; o < 32; o <<= 1) {
+            const double y = __shfl_up_sync(0xffffffffu, x, o);
+            const bool f = __shfl_up_sync(0xffffffffu, flag, o);
+            if (lane >= o && !flag) x = y + x;
+            if (lane >= o) flag = flag || f;
         }
+        const uint32_t next = __shfl_down_sync(0xffffffffu, key, 1);
+        const bool last = valid && (lane == 31 || e == n - 1 || next != key);
+        if (last) part[e] = x;
+    }
+}
+
+__global__ void k_seg_runs(int64_t n, int64_t U, const uint32_t *keys, const uint32_t *hpos, const double *part,
+                           int64_t ubase, int bits_t, int64_t r0, int32_t *uterm, double *usum, int64_t *sup) {
+    const uint32_t tmask = (1u << bits_t) - 1u;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U; u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = hpos[u];
+        const int64_t e = (u + 1 < U) ? (int64_t)hpos[u + 1] : n;
+        double acc = 0.0;
+        for (int64_t c = b >> 5; c <= ((e - 1) >> 5); ++c) {
+            const int64_t end = ((c + 1) << 5) < e ? ((c + 1) << 5) : e;
+            acc += part[end - 1];
+        }
+        const uint32_t key = keys[b];
+        uterm[ubase + u] = (int32_t)(key & tmask);
+        usum[ubase + u] = acc;
+        atomicAdd(reinterpret_cast<unsigned long long *>(sup + r0 + (key >> bits_t)), 1ull);
     }
 }
 
@@ -353,11 +355,12 @@ __global__ void k_if_lens(int32_t D, const uint32_t *cnt2, int64_t *len, int32_t
 }
 
 __global__ void k_if_fill(int64_t n, const uint32_t *order, const int32_t *cclu, const float *cval, int prec,
-                          int32_t *if_cid, float *if_val, uint16_t *if_lp) {
+                          int32_t *if_cid, uint16_t *if_cid16, float *if_val, uint16_t *if_lp) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t e = order[q];
         const float u = cval[e];
         if_cid[q] = cclu[e];
+        if (if_cid16) if_cid16[q] = (uint16_t)cclu[e];
         if_val[q] = u;
         if (prec == SIVF_BF16) {
             if_lp[q] = __bfloat16_as_ushort(__float2bfloat16_rn(u));
@@ -475,7 +478,7 @@ cudaError_t build_inverted_file(sivf_ctx *c) {
     SIVF_CUDA_TRY(radix_sort_pairs(k0, v0, k1, v1, n, c->bits_t + 1, &alt, ws, c->stream));
     if (n > 0) {
         k_if_fill<<<blocks_for(n), TPB, 0, c->stream>>>(n, alt ? v1 : v0, c->cclu, c->cval[cur], (int)c->cfg.prec,
-                                                       c->if_cid, c->if_val, c->if_lp);
+                                                       c->if_cid, c->if_cid16, c->if_val, c->if_lp);
         note_launch();
     }
     SIVF_CUDA_TRY(cudaGetLastError());
@@ -540,7 +543,8 @@ cudaError_t run_update(sivf_ctx *c) {
         uint32_t *tk0 = ws.take<uint32_t>(T), *tv0 = ws.take<uint32_t>(T);
         uint32_t *tk1 = ws.take<uint32_t>(T), *tv1 = ws.take<uint32_t>(T);
         uint32_t *head = ws.take<uint32_t>(T), *uidx = ws.take<uint32_t>(T), *hpos = ws.take<uint32_t>(T);
-        if (!tk0 || !tv0 || !tk1 || !tv1 || !head || !uidx || !hpos) return cudaErrorMemoryAllocation;
+        double *part = ws.take<double>(T);
+        if (!tk0 || !tv0 || !tk1 || !tv1 || !head || !uidx || !hpos || !part) return cudaErrorMemoryAllocation;
         k_expand<<<blocks_for(N * 32), TPB, 0, s>>>(N, perm, c->labels, rrank, r0, tc, toff, c->row_ptr, c->idx,
                                                      c->val, c->bits_t, tk0, tv0);
         note_launch();
@@ -559,9 +563,9 @@ cudaError_t run_update(sivf_ctx *c) {
         note_launch();
         SIVF_CUDA_TRY(cudaStreamSynchronize(s));
         const int64_t U = (int64_t)tail[0] + (int64_t)tail[1];
-        k_segsum<<<blocks_for((U + 31) / 32 * 32), TPB, 0, s>>>(T, U, sk, sv, hpos, ubase, c->bits_t, r0, uterm, usum,
-                                                                  sup);
-        note_launch();
+        k_seg_pieces<<<blocks_for((T + 31) / 32 * 32), TPB, 0, s>>>(T, sk, sv, part);
+        k_seg_runs<<<blocks_for(U), TPB, 0, s>>>(T, U, sk, hpos, part, ubase, c->bits_t, r0, uterm, usum, sup);
+        note_launch(2);
         SIVF_CUDA_TRY(cudaGetLastError());
         ubase += U;
         ws.used = mark;
