@@ -48,7 +48,7 @@ cudaError_t dmalloc(sivf_ctx *c, T **p, size_t n) {
 void free_all(sivf_ctx *c) {
     void *ptrs[] = {c->labels, c->labels_prev, c->own, c->sumv, c->lam, c->lam_prev, c->moving, c->mov_list,
                     c->n_mov_dev, c->snorm, c->snorm_new, c->coff[0], c->coff[1], c->cterm[0], c->cterm[1],
-                    c->cval[0], c->cval[1], c->cclu, c->if_off, c->if_mf0, c->if_cid, c->if_cid16, c->if_val, c->if_lp,
+                    c->cval[0], c->cval[1], c->cclu, c->if_off, c->if_mf0, c->if_cid, c->if_cid16, c->if_pack, c->if_val, c->if_lp,
                     c->ctr, c->obj_dev, c->ws.base};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -166,6 +166,7 @@ sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t
     if (k <= 65536) INIT_CUDA(dmalloc(c, &c->if_cid16, capc + IF_PAD), "alloc");
     INIT_CUDA(dmalloc(c, &c->if_val, capc + IF_PAD), "alloc");
     if (c->cfg.prec != SIVF_FP32) INIT_CUDA(dmalloc(c, &c->if_lp, capc + IF_PAD), "alloc");
+    if (c->cfg.prec != SIVF_FP32 && k <= 65536) INIT_CUDA(dmalloc(c, &c->if_pack, capc + IF_PAD), "alloc");
     INIT_CUDA(dmalloc(c, &c->ctr, 1), "alloc");
     INIT_CUDA(dmalloc(c, &c->obj_dev, 2), "alloc");
     INIT_CUDA(cudaMallocHost(reinterpret_cast<void **>(&c->ctr_host), sizeof(DevCounters)), "alloc host");

@@ -49,6 +49,7 @@ struct AssignParams {
     const int32_t *if_mf0;
     const int32_t *if_cid;
     const uint16_t *if_cid16;
+    const uint32_t *if_pack;   // (id << 16) | bf16/fp16 bits, when k <= 65536 and values are 16-bit
     const void *if_vals;
     const int64_t *coff;
     const int32_t *cterm;
@@ -202,6 +203,7 @@ __device__ __forceinline__ float decode_u(unsigned short b) {
 template <int T, int PREC, bool CID16>
 __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) : 1)
     assign_kernel(AssignParams P) {
+    constexpr bool PACKED = CID16 && PREC != SIVF_FP32;
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int NW = T / 32;
     const int kpad = (P.k + 3) & ~3;
@@ -238,11 +240,12 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
 
         // ---- similarity scan (Algorithm 4, lines 7-13) ----
         // Work items are chunks of CH = 32 * UNR postings of one list
-        // (segment), aligned to 4 entries. A warp takes every NW-th item; lane
-        // l handles postings l, l+32, ... of the chunk (coalesced loads, and on
-        // dense lists the 32 atomics of one step hit consecutive ids, i.e.
-        // distinct banks). Chunks wholly inside the segment take a mask-free
-        // path.
+        // (segment), starting at the segment start; only a segment's last chunk
+        // can be partial. Warp w takes a contiguous block of the items, so the
+        // owning term (and its start, length and value) changes rarely and
+        // stays in registers. Lane l handles postings l, l+32, ... of a chunk:
+        // coalesced loads, and on dense lists the 32 atomics of one step hit
+        // consecutive ids, i.e. distinct banks.
         for (int64_t cb = rb; cb < re; cb += T) {
             const int cn = (int)min((int64_t)T, re - cb);
             int nch = 0;
@@ -253,26 +256,56 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
                 s_start[tid] = (int)o0;
                 s_len[tid] = len;
                 s_vs[tid] = P.val[cb + tid] * FIX_SCALE;  // exact: power-of-two scaling
-                nch = len > 0 ? (((int)o0 & 3) + len + CH - 1) / CH : 0;
+                nch = (len + CH - 1) / CH;
                 c_post_obj += (unsigned long long)len;
             }
             const int incl = block_inclusive_scan_int<T>(nch, warp_i, &s_total);
             s_item[tid] = incl;
             __syncthreads();
             const int items = s_total;
-            // items are visited in increasing order, so the owning term index
-            // only moves forward
-            int h = 0;
-            for (int it = warp; it < items; it += NW) {
-                while (s_item[h] <= it) ++h;
-                const int c = it - (h ? s_item[h - 1] : 0);
-                const int sb = s_start[h], se = sb + s_len[h];
-                const float vs = s_vs[h];
-                const int a0 = (sb & ~3) + c * CH;
-                // one base address per item; the UNR loads use immediate offsets
-                const auto *pc = cid_base<CID16>(P) + (a0 + lane);
-                const auto *pv = val_base<PREC>(P.if_vals) + (a0 + lane);
-                if (a0 >= sb && a0 + CH <= se) {
+            const int per_warp = (items + NW - 1) / NW;
+            const int it0 = warp * per_warp;
+            const int it1 = min(items, it0 + per_warp);
+            int h = 0, h_first = 0, sb = 0, len = 0;
+            float vs = 0.f;
+            bool have = false;
+            for (int it = it0; it < it1; ++it) {
+                if (!have || it >= s_item[h]) {
+                    while (s_item[h] <= it) ++h;
+                    h_first = h ? s_item[h - 1] : 0;
+                    sb = s_start[h];
+                    len = s_len[h];
+                    vs = s_vs[h];
+                    have = true;
+                }
+                const int off = (it - h_first) * CH;  // chunk offset inside the segment
+                const int rem = len - off;            // postings left in the segment
+                if constexpr (PACKED) {
+                    // one 32-bit word per posting: id in the high half, value in the low half
+                    const uint32_t *pw = P.if_pack + (sb + off + lane);
+                    uint32_t ww[UNR];
+                    if (rem >= CH) {
+#pragma unroll
+                        for (int m = 0; m < UNR; ++m) ww[m] = __ldg(pw + 32 * m);
+#pragma unroll
+                        for (int m = 0; m < UNR; ++m)
+                            atomicAdd(&rho[ww[m] >> 16],
+                                      __float2uint_ru(vs * decode_u<PREC>((unsigned short)(ww[m] & 0xFFFFu))));
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < UNR; ++m)
+                            if (32 * m + lane < rem) ww[m] = __ldg(pw + 32 * m);
+#pragma unroll
+                        for (int m = 0; m < UNR; ++m)
+                            if (32 * m + lane < rem)
+                                atomicAdd(&rho[ww[m] >> 16],
+                                          __float2uint_ru(vs * decode_u<PREC>((unsigned short)(ww[m] & 0xFFFFu))));
+                    }
+                    continue;
+                }
+                const auto *pc = cid_base<CID16>(P) + (sb + off + lane);
+                const auto *pv = val_base<PREC>(P.if_vals) + (sb + off + lane);
+                if (rem >= CH) {
                     int cc[UNR];
                     float uu[UNR];
 #pragma unroll
@@ -285,19 +318,16 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
                 } else {
                     int cc[UNR];
                     float uu[UNR];
-                    bool ok[UNR];
 #pragma unroll
                     for (int m = 0; m < UNR; ++m) {
-                        const int pos = a0 + 32 * m + lane;
-                        ok[m] = pos >= sb && pos < se;
-                        if (ok[m]) {
+                        if (32 * m + lane < rem) {
                             cc[m] = (int)__ldg(pc + 32 * m);
                             uu[m] = decode_u<PREC>(__ldg(pv + 32 * m));
                         }
                     }
 #pragma unroll
                     for (int m = 0; m < UNR; ++m)
-                        if (ok[m]) atomicAdd(&rho[cc[m]], __float2uint_ru(vs * uu[m]));
+                        if (32 * m + lane < rem) atomicAdd(&rho[cc[m]], __float2uint_ru(vs * uu[m]));
                 }
             }
             __syncthreads();
@@ -507,6 +537,7 @@ cudaError_t launch_assign(sivf_ctx *c) {
     P.if_mf0 = c->if_mf0;
     P.if_cid = c->if_cid;
     P.if_cid16 = c->if_cid16;
+    P.if_pack = c->if_pack;
     P.if_vals = c->cfg.prec == SIVF_FP32 ? (const void *)c->if_val : (const void *)c->if_lp;
     P.coff = c->coff[c->cur];
     P.cterm = c->cterm[c->cur];

@@ -13,7 +13,8 @@
 //   snorm                 f64[k]        ||s_j|| of the sum behind each centroid
 //   inverted file         if_off int64[D+1], if_mf0 int32[D], if_cid int32[cap],
 //                                        if_cid16 u16[cap] (k <= 65536), if_val f32[cap],
-//                                        if_lp u16[cap] (bf16/fp16 copy)
+//                                        if_lp u16[cap] (bf16/fp16 copy), if_pack u32[cap]
+//                                        (id << 16 | bf16/fp16 value, read by the scan)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -110,6 +111,7 @@ struct sivf_ctx {
     int32_t *if_mf0 = nullptr;
     int32_t *if_cid = nullptr;
     uint16_t *if_cid16 = nullptr;  // 16-bit copy of if_cid when k <= 65536 (read by the scan)
+    uint32_t *if_pack = nullptr;   // (id << 16) | 16-bit value, for bf16/fp16 postings when k <= 65536
     float *if_val = nullptr;
     uint16_t *if_lp = nullptr;
     int64_t if_nnz = 0;

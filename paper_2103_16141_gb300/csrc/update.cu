@@ -215,8 +215,11 @@ __global__ void k_seg_pieces(int64_t n, const uint32_t *keys, const uint32_t *va
     }
 }
 
+// Runs arrive sorted by (cluster rank, term): the first and the last run of
+// each cluster record where its unique entries begin and end (no atomics).
 __global__ void k_seg_runs(int64_t n, int64_t U, const uint32_t *keys, const uint32_t *hpos, const double *part,
-                           int64_t ubase, int bits_t, int64_t r0, int32_t *uterm, double *usum, int64_t *sup) {
+                           int64_t ubase, int bits_t, int64_t r0, int32_t *uterm, double *usum, int64_t *ubeg,
+                           int64_t *uend) {
     const uint32_t tmask = (1u << bits_t) - 1u;
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U; u += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = hpos[u];
@@ -227,18 +230,20 @@ __global__ void k_seg_runs(int64_t n, int64_t U, const uint32_t *keys, const uin
             acc += part[end - 1];
         }
         const uint32_t key = keys[b];
+        const uint32_t r = key >> bits_t;
         uterm[ubase + u] = (int32_t)(key & tmask);
         usum[ubase + u] = acc;
-        atomicAdd(reinterpret_cast<unsigned long long *>(sup + r0 + (key >> bits_t)), 1ull);
+        if (u == 0 || (keys[hpos[u - 1]] >> bits_t) != r) ubeg[r0 + r] = ubase + u;
+        if (u + 1 == U || (keys[e] >> bits_t) != r) uend[r0 + r] = ubase + u + 1;
     }
 }
 
 // ---------------- u3 / u4: new centroid rows ----------------
 
-__global__ void k_new_sizes(int32_t k, const int64_t *flag, const int64_t *rrank, const int64_t *sup,
-                            const int64_t *coff_old, int64_t *sz) {
+__global__ void k_new_sizes(int32_t k, const int64_t *flag, const int64_t *rrank, const int64_t *supoff,
+                            const int64_t *supend, const int64_t *coff_old, int64_t *sz) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < k) sz[j] = flag[j] ? sup[rrank[j]] : coff_old[j + 1] - coff_old[j];
+    if (j < k) sz[j] = flag[j] ? supend[rrank[j]] - supoff[rrank[j]] : coff_old[j + 1] - coff_old[j];
 }
 
 // One CTA (WR_THREADS) per cluster. Recomputed clusters: ||s|| in FP64 with
@@ -260,7 +265,7 @@ __device__ __forceinline__ double block_sum_fixed(double x, double *sh) {
 }
 
 __global__ void __launch_bounds__(WR_THREADS) k_write_rows(
-    int32_t k, const int64_t *flag, const int64_t *rrank, const int64_t *supoff, const int64_t *sup,
+    int32_t k, const int64_t *flag, const int64_t *rrank, const int64_t *supoff, const int64_t *supend,
     const int32_t *uterm, const double *usum, const int64_t *cnt, const int64_t *coff_old, const int32_t *cterm_old,
     const float *cval_old, const double *snorm_old, const int64_t *coff_new, int32_t *cterm_new, float *cval_new,
     int32_t *cclu_new, double *snorm_new, double *jA, double *jU) {
@@ -271,7 +276,7 @@ __global__ void __launch_bounds__(WR_THREADS) k_write_rows(
     const int64_t cb = coff_old[j], ce = coff_old[j + 1];
     if (flag[j]) {
         const int64_t r = rrank[j];
-        const int64_t ub = supoff[r], n = sup[r];
+        const int64_t ub = supoff[r], n = supend[r] - supoff[r];
         double ss = 0.0;
         for (int64_t q = threadIdx.x; q < n; q += WR_THREADS) ss += usum[ub + q] * usum[ub + q];
         const double nrm = sqrt(block_sum_fixed(ss, sh));
@@ -355,20 +360,24 @@ __global__ void k_if_lens(int32_t D, const uint32_t *cnt2, int64_t *len, int32_t
 }
 
 __global__ void k_if_fill(int64_t n, const uint32_t *order, const int32_t *cclu, const float *cval, int prec,
-                          int32_t *if_cid, uint16_t *if_cid16, float *if_val, uint16_t *if_lp) {
+                          int32_t *if_cid, uint16_t *if_cid16, uint32_t *if_pack, float *if_val,
+                          uint16_t *if_lp) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t e = order[q];
         const float u = cval[e];
         if_cid[q] = cclu[e];
         if (if_cid16) if_cid16[q] = (uint16_t)cclu[e];
         if_val[q] = u;
+        unsigned short lp = 0;
         if (prec == SIVF_BF16) {
-            if_lp[q] = __bfloat16_as_ushort(__float2bfloat16_rn(u));
+            lp = __bfloat16_as_ushort(__float2bfloat16_rn(u));
+            if_lp[q] = lp;
         } else if (prec == SIVF_FP16) {
-            unsigned short h = __half_as_ushort(__float2half_rn(u * FP16_SCALE));
-            if (h == 0 && u > 0.0f) h = 1;  // keep every posting strictly positive
-            if_lp[q] = h;
+            lp = __half_as_ushort(__float2half_rn(u * FP16_SCALE));
+            if (lp == 0 && u > 0.0f) lp = 1;  // keep every posting strictly positive
+            if_lp[q] = lp;
         }
+        if (if_pack) if_pack[q] = ((uint32_t)cclu[e] << 16) | (uint32_t)lp;
     }
 }
 
@@ -478,7 +487,7 @@ cudaError_t build_inverted_file(sivf_ctx *c) {
     SIVF_CUDA_TRY(radix_sort_pairs(k0, v0, k1, v1, n, c->bits_t + 1, &alt, ws, c->stream));
     if (n > 0) {
         k_if_fill<<<blocks_for(n), TPB, 0, c->stream>>>(n, alt ? v1 : v0, c->cclu, c->cval[cur], (int)c->cfg.prec,
-                                                       c->if_cid, c->if_cid16, c->if_val, c->if_lp);
+                                                       c->if_cid, c->if_cid16, c->if_pack, c->if_val, c->if_lp);
         note_launch();
     }
     SIVF_CUDA_TRY(cudaGetLastError());
@@ -520,12 +529,14 @@ cudaError_t run_update(sivf_ctx *c) {
     SIVF_CUDA_TRY(cudaStreamSynchronize(s));
 
     // u2: per (cluster, term) sums for the recomputed clusters, in rank batches
-    int64_t *sup = ws.take<int64_t>((size_t)nrec + 1), *supoff = ws.take<int64_t>((size_t)nrec + 1);
+    int64_t *supoff = ws.take<int64_t>((size_t)nrec + 1), *supend = ws.take<int64_t>((size_t)nrec + 1);
     const int64_t ucap = c->nnz + 1;
     int32_t *uterm = ws.take<int32_t>((size_t)ucap);
     double *usum = ws.take<double>((size_t)ucap);
-    if (!sup || !supoff || !uterm || !usum) return cudaErrorMemoryAllocation;
-    SIVF_CUDA_TRY(cudaMemsetAsync(sup, 0, sizeof(int64_t) * (nrec + 1), s));
+    if (!supoff || !supend || !uterm || !usum) return cudaErrorMemoryAllocation;
+    // a cluster whose members are all empty rows has no entries: begin = end = 0
+    SIVF_CUDA_TRY(cudaMemsetAsync(supoff, 0, sizeof(int64_t) * (nrec + 1), s));
+    SIVF_CUDA_TRY(cudaMemsetAsync(supend, 0, sizeof(int64_t) * (nrec + 1), s));
     const int rbits_max = 32 - c->bits_t;
     const int64_t batch = rbits_max >= 31 ? (int64_t)1 << 31 : (int64_t)1 << rbits_max;
     int64_t ubase = 0, moved_nnz = 0;
@@ -564,16 +575,16 @@ cudaError_t run_update(sivf_ctx *c) {
         SIVF_CUDA_TRY(cudaStreamSynchronize(s));
         const int64_t U = (int64_t)tail[0] + (int64_t)tail[1];
         k_seg_pieces<<<blocks_for((T + 31) / 32 * 32), TPB, 0, s>>>(T, sk, sv, part);
-        k_seg_runs<<<blocks_for(U), TPB, 0, s>>>(T, U, sk, hpos, part, ubase, c->bits_t, r0, uterm, usum, sup);
+        k_seg_runs<<<blocks_for(U), TPB, 0, s>>>(T, U, sk, hpos, part, ubase, c->bits_t, r0, uterm, usum, supoff,
+                                                  supend);
         note_launch(2);
         SIVF_CUDA_TRY(cudaGetLastError());
         ubase += U;
         ws.used = mark;
     }
-    SIVF_CUDA_TRY(scan_exclusive_i64(sup, supoff, nrec, nullptr, ws, s));
 
     // u3/u4: new cluster-major rows
-    k_new_sizes<<<blocks_for(k), TPB, 0, s>>>(k, flag, rrank, sup, c->coff[old], sz);
+    k_new_sizes<<<blocks_for(k), TPB, 0, s>>>(k, flag, rrank, supoff, supend, c->coff[old], sz);
     note_launch();
     SIVF_CUDA_TRY(scan_exclusive_i64(sz, c->coff[nw], k, tot_d, ws, s));
     SIVF_CUDA_TRY(cudaMemcpyAsync(c->coff[nw] + k, tot_d, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
@@ -582,7 +593,7 @@ cudaError_t run_update(sivf_ctx *c) {
     SIVF_CUDA_TRY(cudaStreamSynchronize(s));
     if (newn > c->cap_c || newn >= 0x7FFFFFFFll - 2 * IF_PAD) return cudaErrorMemoryAllocation;
     k_write_rows<<<(unsigned)k, WR_THREADS, 0, s>>>(
-        k, flag, rrank, supoff, sup, uterm, usum, cnt, c->coff[old], c->cterm[old], c->cval[old], c->snorm,
+        k, flag, rrank, supoff, supend, uterm, usum, cnt, c->coff[old], c->cterm[old], c->cval[old], c->snorm,
         c->coff[nw], c->cterm[nw], c->cval[nw], c->cclu, c->snorm_new, jAd, jUd);
     note_launch();
     k_sum2<<<1, 1024, 0, s>>>(k, jAd, jUd, c->obj_dev);
