@@ -182,6 +182,57 @@ sivf_status sivf_get_stats(sivf_ctx *ctx, sivf_stats *out);
  * valid until the next call on ctx. Accepts NULL (returns a static string). */
 const char *sivf_last_error(const sivf_ctx *ctx);
 
+/*
+ * Batched independent instances (one context, one assignment launch and one
+ * update per iteration for all of them).
+ *
+ * sivf_instance_desc — one clustering problem: N objects over D terms, k
+ * clusters, its own CSR (DEVICE, same rules as sivf_init; copied at init,
+ * so the caller may free it afterwards) and k distinct seed object ids
+ * (HOST, local to the instance, copied).
+ */
+typedef struct {
+    int64_t N;
+    int32_t D;
+    int32_t k;
+    const int64_t *row_ptr;
+    const int32_t *idx;
+    const float *val;
+    const int32_t *init_ids;
+} sivf_instance_desc;
+
+/*
+ * sivf_batch_init — one context for n_inst independent instances. Internally
+ * the instances are laid side by side (disjoint object, term and cluster
+ * ranges); every assignment and update step covers all of them, and each
+ * object is only compared with its own instance's centroids. sivf_assign,
+ * sivf_update, sivf_get_stats and sivf_reseed (global seed ids, instance by
+ * instance) work on the whole batch; the other getters see the concatenation.
+ * Errors as sivf_init.
+ */
+sivf_status sivf_batch_init(sivf_ctx **out, const sivf_config *cfg, int32_t n_inst, const sivf_instance_desc *descs,
+                            void *stream);
+
+/*
+ * sivf_batch_run — Algorithm 1 for every instance at once: iterate until each
+ * instance has had an assignment (r > 1) that changes none of its labels, or
+ * max_iter assignments. An instance that converged stays converged (all its
+ * clusters are invariant, so its objects keep their labels at no scan cost).
+ *   iters_out     : HOST int32[n_inst], may be NULL; assignment steps until the
+ *                   instance converged (max_iter if it did not).
+ *   objective_out : HOST double[n_inst], may be NULL; the instance's objective
+ *                   sum of cosines at its last update.
+ */
+sivf_status sivf_batch_run(sivf_ctx *ctx, int32_t max_iter, int32_t *iters_out, double *objective_out);
+
+/* sivf_batch_get_labels — instance inst's N labels, local cluster ids, to HOST dst. */
+sivf_status sivf_batch_get_labels(sivf_ctx *ctx, int32_t inst, int32_t *dst);
+
+/* sivf_batch_instance_stats — instance inst's changed count of the last
+ * assignment and its objectives of the last update (HOST outs, may be NULL). */
+sivf_status sivf_batch_instance_stats(sivf_ctx *ctx, int32_t inst, int64_t *changed, double *objective_assign,
+                                      double *objective_update);
+
 /* sivf_destroy — free all library-owned device memory. Accepts NULL. */
 void sivf_destroy(sivf_ctx *ctx);
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <utility>
@@ -49,7 +50,8 @@ void free_all(sivf_ctx *c) {
     void *ptrs[] = {c->labels, c->labels_prev, c->own, c->sumv, c->lam, c->lam_prev, c->moving, c->mov_list,
                     c->n_mov_dev, c->snorm, c->snorm_new, c->coff[0], c->coff[1], c->cterm[0], c->cterm[1],
                     c->cval[0], c->cval[1], c->cclu, c->if_off, c->if_mf0, c->if_cid, c->if_cid16, c->if_pack, c->if_val, c->if_lp,
-                    c->ctr, c->obj_dev, c->ws.base};
+                    c->ctr, c->obj_dev, c->ws.base, c->inst_obj, c->inst_k, c->mov_beg, c->clu_koff,
+                    c->inst_changed, c->own_row_ptr, c->own_idx, c->own_val};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->ctr_host) cudaFreeHost(c->ctr_host);
@@ -73,27 +75,27 @@ void pick_assign_config(sivf_ctx *c) {
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t D, int32_t k,
-                      const int64_t *row_ptr, const int32_t *idx, const float *val, const int32_t *init_ids,
-                      void *stream) {
-    if (!out) return SIVF_ERR_INVALID_ARG;
-    *out = nullptr;
-    if (N < 1 || N > 0x7FFFFFFFll || D < 1 || D > (1 << 30) || k < 1 || (int64_t)k > N || !row_ptr || !idx || !val ||
-        !init_ids)
-        return SIVF_ERR_INVALID_ARG;
-    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16)) return SIVF_ERR_INVALID_ARG;
-    {
-        std::vector<char> seen((size_t)N, 0);
-        for (int32_t j = 0; j < k; ++j) {
-            int32_t d = init_ids[j];
-            if (d < 0 || (int64_t)d >= N || seen[(size_t)d]) return SIVF_ERR_INVALID_ARG;
-            seen[(size_t)d] = 1;
-        }
-    }
+// Shared tail of sivf_init and sivf_batch_init: allocate every device array,
+// validate the (possibly concatenated) CSR, seed the centroids and build the
+// first inverted file. Instance tables are host vectors of n_inst + 1 offsets.
+// owned_* (non-null for batch contexts) are adopted by the context.
+sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t D, int32_t k,
+                       const int64_t *row_ptr, const int32_t *idx, const float *val, const int32_t *init_ids,
+                       void *stream, const std::vector<int64_t> &inst_obj, const std::vector<int32_t> &inst_k,
+                       const std::vector<int32_t> &inst_d, int64_t *owned_row_ptr, int32_t *owned_idx,
+                       float *owned_val) {
     sivf_ctx *c = new (std::nothrow) sivf_ctx();
-    if (!c) return SIVF_ERR_OOM;
+    if (!c) {
+        cudaFree(owned_row_ptr);
+        cudaFree(owned_idx);
+        cudaFree(owned_val);
+        return SIVF_ERR_OOM;
+    }
+    c->own_row_ptr = owned_row_ptr;
+    c->own_idx = owned_idx;
+    c->own_val = owned_val;
     if (cfg) {
         c->cfg = *cfg;
     } else {
@@ -108,9 +110,19 @@ sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t
     c->row_ptr = row_ptr;
     c->idx = idx;
     c->val = val;
+    c->n_inst = (int32_t)inst_obj.size() - 1;
+    c->inst_obj_h = inst_obj;
+    c->inst_k_h = inst_k;
+    c->inst_d_h = inst_d;
+    c->inst_changed_h.assign((size_t)c->n_inst, 0);
+    c->inst_obj_assign_h.assign((size_t)c->n_inst, 0.0);
+    c->inst_obj_update_h.assign((size_t)c->n_inst, 0.0);
+    c->kmax = 0;
+    for (int32_t m = 0; m < c->n_inst; ++m) c->kmax = std::max(c->kmax, inst_k[(size_t)m + 1] - inst_k[(size_t)m]);
     c->bits_t = bits_for((uint64_t)(D - 1));
     if (c->bits_t < 1) c->bits_t = 1;
     if (c->bits_t > 30) {
+        free_all(c);
         delete c;
         return SIVF_ERR_INVALID_ARG;
     }
@@ -135,12 +147,14 @@ sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t
     INIT_CUDA(cudaMemcpyAsync(&first, row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream), "read row_ptr");
     INIT_CUDA(cudaStreamSynchronize(c->stream), "sync");
     if (first != 0 || nnz < 0 || nnz >= 0x7FFFFFFFll) {
+        free_all(c);
         delete c;
         return SIVF_ERR_BAD_CSR;
     }
     c->nnz = nnz;
     c->cap_c = 2 * nnz + 1024;
     const int64_t capc = c->cap_c;
+    const int32_t ni = c->n_inst;
     INIT_CUDA(dmalloc(c, &c->labels, N), "alloc");
     INIT_CUDA(dmalloc(c, &c->labels_prev, N), "alloc");
     INIT_CUDA(dmalloc(c, &c->own, N), "alloc");
@@ -152,6 +166,11 @@ sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t
     INIT_CUDA(dmalloc(c, &c->n_mov_dev, 1), "alloc");
     INIT_CUDA(dmalloc(c, &c->snorm, k), "alloc");
     INIT_CUDA(dmalloc(c, &c->snorm_new, k), "alloc");
+    INIT_CUDA(dmalloc(c, &c->inst_obj, (size_t)ni + 1), "alloc");
+    INIT_CUDA(dmalloc(c, &c->inst_k, (size_t)ni + 1), "alloc");
+    INIT_CUDA(dmalloc(c, &c->mov_beg, (size_t)ni + 1), "alloc");
+    INIT_CUDA(dmalloc(c, &c->clu_koff, k), "alloc");
+    INIT_CUDA(dmalloc(c, &c->inst_changed, ni), "alloc");
     for (int b = 0; b < 2; ++b) {
         INIT_CUDA(dmalloc(c, &c->coff[b], (size_t)k + 1), "alloc");
         INIT_CUDA(dmalloc(c, &c->cterm[b], capc), "alloc");
@@ -160,15 +179,15 @@ sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t
     INIT_CUDA(dmalloc(c, &c->cclu, capc), "alloc");
     INIT_CUDA(dmalloc(c, &c->if_off, (size_t)D + 1), "alloc");
     INIT_CUDA(dmalloc(c, &c->if_mf0, D), "alloc");
-    // the scan reads aligned groups of 4 postings: up to 3 entries past the
-    // last list, so the posting arrays carry a small tail pad
+    // posting arrays carry a small tail pad
     INIT_CUDA(dmalloc(c, &c->if_cid, capc + IF_PAD), "alloc");
-    if (k <= 65536) INIT_CUDA(dmalloc(c, &c->if_cid16, capc + IF_PAD), "alloc");
+    const bool ids16 = c->kmax <= 65536;
+    if (ids16) INIT_CUDA(dmalloc(c, &c->if_cid16, capc + IF_PAD), "alloc");
     INIT_CUDA(dmalloc(c, &c->if_val, capc + IF_PAD), "alloc");
     if (c->cfg.prec != SIVF_FP32) INIT_CUDA(dmalloc(c, &c->if_lp, capc + IF_PAD), "alloc");
-    if (c->cfg.prec != SIVF_FP32 && k <= 65536) INIT_CUDA(dmalloc(c, &c->if_pack, capc + IF_PAD), "alloc");
+    if (c->cfg.prec != SIVF_FP32 && ids16) INIT_CUDA(dmalloc(c, &c->if_pack, capc + IF_PAD), "alloc");
     INIT_CUDA(dmalloc(c, &c->ctr, 1), "alloc");
-    INIT_CUDA(dmalloc(c, &c->obj_dev, 2), "alloc");
+    INIT_CUDA(dmalloc(c, &c->obj_dev, 2 * (size_t)ni), "alloc");
     INIT_CUDA(cudaMallocHost(reinterpret_cast<void **>(&c->ctr_host), sizeof(DevCounters)), "alloc host");
     {
         // workspace: max of the update's two phases, plus primitive scratch
@@ -187,6 +206,18 @@ sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t
         c->ws.cap = ws;
     }
     for (auto &ev : c->ev) INIT_CUDA(cudaEventCreate(&ev), "event");
+    {
+        std::vector<int32_t> koff((size_t)k);
+        for (int32_t m = 0; m < ni; ++m)
+            for (int32_t j = inst_k[(size_t)m]; j < inst_k[(size_t)m + 1]; ++j) koff[(size_t)j] = inst_k[(size_t)m];
+        INIT_CUDA(cudaMemcpyAsync(c->inst_obj, inst_obj.data(), sizeof(int64_t) * (ni + 1), cudaMemcpyHostToDevice,
+                                  c->stream), "copy");
+        INIT_CUDA(cudaMemcpyAsync(c->inst_k, inst_k.data(), sizeof(int32_t) * (ni + 1), cudaMemcpyHostToDevice,
+                                  c->stream), "copy");
+        INIT_CUDA(cudaMemcpyAsync(c->clu_koff, koff.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, c->stream),
+                  "copy");
+        INIT_CUDA(cudaStreamSynchronize(c->stream), "sync");
+    }
 
     // validate the CSR and compute per-object value sums
     c->launch_base = g_launches;
@@ -197,47 +228,160 @@ sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t
         delete c;
         return SIVF_ERR_BAD_CSR;
     }
-    // state: no labels, no own scores, every cluster moving
-    INIT_CUDA(cudaMemsetAsync(c->labels, 0xFF, sizeof(int32_t) * N, c->stream), "memset");
-    INIT_CUDA(cudaMemsetAsync(c->labels_prev, 0xFF, sizeof(int32_t) * N, c->stream), "memset");
-    INIT_CUDA(cudaMemsetAsync(c->own, 0xFF, sizeof(uint32_t) * N, c->stream), "memset");
-    INIT_CUDA(cudaMemsetAsync(c->lam, 0, k, c->stream), "memset");
-    INIT_CUDA(cudaMemsetAsync(c->lam_prev, 0, k, c->stream), "memset");
-    INIT_CUDA(cudaMemsetAsync(c->moving, 1, k, c->stream), "memset");
-    INIT_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream), "memset");
     {
-        std::vector<int32_t> ids((size_t)k);
-        for (int32_t j = 0; j < k; ++j) ids[(size_t)j] = j;
-        INIT_CUDA(cudaMemcpyAsync(c->mov_list, ids.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, c->stream),
-                  "copy");
-        INIT_CUDA(cudaMemcpyAsync(c->n_mov_dev, &k, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream), "copy");
         int32_t *ids_dev = c->ws.take<int32_t>((size_t)k);
         INIT_CUDA(ids_dev ? cudaSuccess : cudaErrorMemoryAllocation, "ws");
         INIT_CUDA(cudaMemcpyAsync(ids_dev, init_ids, sizeof(int32_t) * k, cudaMemcpyHostToDevice, c->stream), "copy");
-        INIT_CUDA(cudaStreamSynchronize(c->stream), "sync");
-        // copy the seed rows (cluster-major), then the first inverted file
-        INIT_CUDA(init_centroids(c, ids_dev), "init centroids");
+        // state: no labels, no own scores, every cluster moving; seed rows and
+        // the first inverted file
+        INIT_CUDA(reseed_dev(c, ids_dev), "seed");
     }
-    INIT_CUDA(build_inverted_file(c), "build inverted file");
     INIT_CUDA(cudaStreamSynchronize(c->stream), "sync");
+    c->ws.reset();
     c->stats.centroid_nnz = c->c_nnz;
 #undef INIT_CUDA
     *out = c;
     return SIVF_OK;
 }
 
+bool distinct_ids(const int32_t *ids, int32_t k, int64_t N) {
+    std::vector<char> seen((size_t)N, 0);
+    for (int32_t j = 0; j < k; ++j) {
+        const int32_t d = ids[j];
+        if (d < 0 || (int64_t)d >= N || seen[(size_t)d]) return false;
+        seen[(size_t)d] = 1;
+    }
+    return true;
+}
+
+__global__ void k_concat_rows(int64_t n, const int64_t *src, int64_t nnz_off, int64_t *dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i] + nnz_off;
+}
+
+__global__ void k_concat_terms(int64_t n, const int32_t *src, int32_t d_off, int32_t D, int32_t *dst, int *bad) {
+    for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < n; h += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t t = src[h];
+        if (t < 0 || t >= D) atomicOr(bad, 1);
+        dst[h] = (t < 0 || t >= D) ? -1 : t + d_off;  // -1 fails validation later
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t D, int32_t k,
+                      const int64_t *row_ptr, const int32_t *idx, const float *val, const int32_t *init_ids,
+                      void *stream) {
+    if (!out) return SIVF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (N < 1 || N > 0x7FFFFFFFll || D < 1 || D > (1 << 30) || k < 1 || (int64_t)k > N || !row_ptr || !idx || !val ||
+        !init_ids)
+        return SIVF_ERR_INVALID_ARG;
+    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16)) return SIVF_ERR_INVALID_ARG;
+    if (!distinct_ids(init_ids, k, N)) return SIVF_ERR_INVALID_ARG;
+    return create_ctx(out, cfg, N, D, k, row_ptr, idx, val, init_ids, stream, {0, N}, {0, k}, {0, D}, nullptr,
+                      nullptr, nullptr);
+}
+
+sivf_status sivf_batch_init(sivf_ctx **out, const sivf_config *cfg, int32_t n_inst, const sivf_instance_desc *descs,
+                            void *stream) {
+    if (!out) return SIVF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_inst < 1 || n_inst > 65536 || !descs) return SIVF_ERR_INVALID_ARG;
+    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16)) return SIVF_ERR_INVALID_ARG;
+    std::vector<int64_t> inst_obj(1, 0);
+    std::vector<int32_t> inst_k(1, 0), inst_d(1, 0);
+    for (int32_t m = 0; m < n_inst; ++m) {
+        const sivf_instance_desc &d = descs[m];
+        if (d.N < 1 || d.D < 1 || d.k < 1 || (int64_t)d.k > d.N || !d.row_ptr || !d.idx || !d.val || !d.init_ids)
+            return SIVF_ERR_INVALID_ARG;
+        if (!distinct_ids(d.init_ids, d.k, d.N)) return SIVF_ERR_INVALID_ARG;
+        if (inst_obj.back() + d.N > 0x7FFFFFFFll || (int64_t)inst_k.back() + d.k > 0x7FFFFFFFll ||
+            (int64_t)inst_d.back() + d.D > (1 << 30))
+            return SIVF_ERR_INVALID_ARG;
+        inst_obj.push_back(inst_obj.back() + d.N);
+        inst_k.push_back(inst_k.back() + d.k);
+        inst_d.push_back(inst_d.back() + d.D);
+    }
+    const int64_t N = inst_obj.back();
+    const int32_t K = inst_k.back(), Dt = inst_d.back();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // instance sizes (nnz) from each row_ptr[N]
+    std::vector<int64_t> nnz_off(1, 0);
+    for (int32_t m = 0; m < n_inst; ++m) {
+        int64_t nz = 0, f = 0;
+        if (cudaMemcpyAsync(&nz, descs[m].row_ptr + descs[m].N, sizeof(int64_t), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(&f, descs[m].row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return SIVF_ERR_CUDA;
+        if (f != 0 || nz < 0) return SIVF_ERR_BAD_CSR;
+        nnz_off.push_back(nnz_off.back() + nz);
+    }
+    const int64_t nnz = nnz_off.back();
+    if (nnz >= 0x7FFFFFFFll) return SIVF_ERR_INVALID_ARG;
+    // concatenated CSR: terms of instance m shifted by its term offset
+    int64_t *rp = nullptr;
+    int32_t *ix = nullptr;
+    float *vl = nullptr;
+    int *bad = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(rp);
+        cudaFree(ix);
+        cudaFree(vl);
+        cudaFree(bad);
+    };
+    if (cudaMalloc(&rp, sizeof(int64_t) * (N + 1)) != cudaSuccess || cudaMalloc(&ix, sizeof(int32_t) * (nnz + 1)) != cudaSuccess ||
+        cudaMalloc(&vl, sizeof(float) * (nnz + 1)) != cudaSuccess || cudaMalloc(&bad, sizeof(int)) != cudaSuccess) {
+        cleanup();
+        return SIVF_ERR_OOM;
+    }
+    bool ok = cudaMemsetAsync(bad, 0, sizeof(int), s) == cudaSuccess;
+    for (int32_t m = 0; m < n_inst && ok; ++m) {
+        const sivf_instance_desc &d = descs[m];
+        const int64_t nz = nnz_off[(size_t)m + 1] - nnz_off[(size_t)m];
+        k_concat_rows<<<(unsigned)std::min<int64_t>((d.N + 255) / 256 + 1, 65535), 256, 0, s>>>(
+            d.N, d.row_ptr, nnz_off[(size_t)m], rp + inst_obj[(size_t)m]);
+        if (nz > 0) {
+            k_concat_terms<<<(unsigned)std::min<int64_t>((nz + 255) / 256, 65535), 256, 0, s>>>(
+                nz, d.idx, inst_d[(size_t)m], d.D, ix + nnz_off[(size_t)m], bad);
+            ok = cudaMemcpyAsync(vl + nnz_off[(size_t)m], d.val, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s) ==
+                 cudaSuccess;
+        }
+        note_launch(nz > 0 ? 2 : 1);
+    }
+    int bad_h = 0;
+    ok = ok && cudaMemcpyAsync(rp + N, &nnz, sizeof(int64_t), cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(s) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+    cudaFree(bad);
+    bad = nullptr;
+    if (!ok) {
+        cleanup();
+        return SIVF_ERR_CUDA;
+    }
+    if (bad_h) {
+        cleanup();
+        return SIVF_ERR_BAD_CSR;
+    }
+    std::vector<int32_t> ids((size_t)K);
+    for (int32_t m = 0; m < n_inst; ++m)
+        for (int32_t j = 0; j < descs[m].k; ++j)
+            ids[(size_t)inst_k[(size_t)m] + j] = descs[m].init_ids[j] + (int32_t)inst_obj[(size_t)m];
+    return create_ctx(out, cfg, N, Dt, K, rp, ix, vl, ids.data(), stream, inst_obj, inst_k, inst_d, rp, ix, vl);
+}
+
 sivf_status sivf_reseed(sivf_ctx *c, const int32_t *init_ids) {
     sivf_status st = check_usable(c);
     if (st != SIVF_OK) return st;
     if (!init_ids) return fail(c, SIVF_ERR_INVALID_ARG, "init_ids is NULL");
-    {
-        std::vector<char> seen((size_t)c->N, 0);
-        for (int32_t j = 0; j < c->k; ++j) {
-            int32_t d = init_ids[j];
-            if (d < 0 || (int64_t)d >= c->N || seen[(size_t)d]) return fail(c, SIVF_ERR_INVALID_ARG, "bad init ids");
-            seen[(size_t)d] = 1;
-        }
-    }
+    if (!distinct_ids(init_ids, c->k, c->N)) return fail(c, SIVF_ERR_INVALID_ARG, "bad init ids");
+    for (int32_t m = 0; m < c->n_inst; ++m)  // each seed must be an object of its cluster's instance
+        for (int32_t j = c->inst_k_h[(size_t)m]; j < c->inst_k_h[(size_t)m + 1]; ++j)
+            if (init_ids[j] < c->inst_obj_h[(size_t)m] || init_ids[j] >= c->inst_obj_h[(size_t)m + 1])
+                return fail(c, SIVF_ERR_INVALID_ARG, "seed outside its instance");
     c->ws.reset();
     int32_t *ids_dev = c->ws.take<int32_t>((size_t)c->k);
     if (!ids_dev) return cuda_fail(c, cudaErrorMemoryAllocation, "workspace");
@@ -263,6 +407,7 @@ sivf_status sivf_assign(sivf_ctx *c, int64_t *n_changed) {
     c->iter += 1;
     API_CUDA(c, cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream), "memset");
     API_CUDA(c, cudaMemsetAsync(c->moving, 0, c->k, c->stream), "memset");
+    API_CUDA(c, cudaMemsetAsync(c->inst_changed, 0, sizeof(unsigned long long) * c->n_inst, c->stream), "memset");
     int32_t nmp = 0;
     API_CUDA(c, cudaMemcpyAsync(&nmp, c->n_mov_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream), "copy");
     API_CUDA(c, cudaEventRecord(c->ev[0], c->stream), "event");
@@ -270,7 +415,11 @@ sivf_status sivf_assign(sivf_ctx *c, int64_t *n_changed) {
     API_CUDA(c, launch_finalize_assign(c), "finalize kernel");
     API_CUDA(c, cudaEventRecord(c->ev[1], c->stream), "event");
     API_CUDA(c, cudaMemcpyAsync(c->ctr_host, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->stream), "copy");
+    if (c->n_inst > 1)
+        API_CUDA(c, cudaMemcpyAsync(c->inst_changed_h.data(), c->inst_changed, sizeof(unsigned long long) * c->n_inst,
+                                    cudaMemcpyDeviceToHost, c->stream), "copy");
     API_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
+    if (c->n_inst == 1) c->inst_changed_h[0] = c->ctr_host->changed;
     float ms = 0.f;
     API_CUDA(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]), "elapsed");
     const DevCounters &h = *c->ctr_host;
@@ -304,13 +453,21 @@ sivf_status sivf_update(sivf_ctx *c) {
     API_CUDA(c, cudaEventRecord(c->ev[2], c->stream), "event");
     API_CUDA(c, run_update(c), "update");
     API_CUDA(c, cudaEventRecord(c->ev[3], c->stream), "event");
-    double obj[2] = {0, 0};
-    API_CUDA(c, cudaMemcpyAsync(obj, c->obj_dev, sizeof(obj), cudaMemcpyDeviceToHost, c->stream), "copy");
+    std::vector<double> obj(2 * (size_t)c->n_inst, 0.0);
+    API_CUDA(c, cudaMemcpyAsync(obj.data(), c->obj_dev, sizeof(double) * obj.size(), cudaMemcpyDeviceToHost,
+                                c->stream), "copy");
     API_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
     float ms = 0.f;
     API_CUDA(c, cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]), "elapsed");
-    c->stats.objective_assign = obj[0];
-    c->stats.objective_update = obj[1];
+    double ja = 0.0, ju = 0.0;
+    for (int32_t m = 0; m < c->n_inst; ++m) {
+        c->inst_obj_assign_h[(size_t)m] = obj[2 * (size_t)m];
+        c->inst_obj_update_h[(size_t)m] = obj[2 * (size_t)m + 1];
+        ja += obj[2 * (size_t)m];
+        ju += obj[2 * (size_t)m + 1];
+    }
+    c->stats.objective_assign = ja;
+    c->stats.objective_update = ju;
     c->stats.ms_update = ms;
     c->stats.centroid_nnz = c->c_nnz;
     c->needs_update = false;
@@ -335,7 +492,7 @@ sivf_status sivf_run(sivf_ctx *c, int32_t max_iter, int32_t *iters_out, double *
         if (c->iter > 1 && changed == 0) break;
         st = sivf_update(c);
         if (st != SIVF_OK) return st;
-        obj = c->stats.objective_assign;
+        obj = c->stats.objective_update;
     }
     if (iters_out) *iters_out = done;
     if (objective_out) *objective_out = obj;
@@ -431,6 +588,65 @@ sivf_status sivf_get_stats(sivf_ctx *c, sivf_stats *out) {
 const char *sivf_last_error(const sivf_ctx *c) {
     if (!c) return kNoCtx;
     return c->err.c_str();
+}
+
+sivf_status sivf_batch_run(sivf_ctx *c, int32_t max_iter, int32_t *iters_out, double *objective_out) {
+    sivf_status st = check_usable(c);
+    if (st != SIVF_OK) return st;
+    if (max_iter < 0) return fail(c, SIVF_ERR_INVALID_ARG, "max_iter < 0");
+    const size_t ni = (size_t)c->n_inst;
+    std::vector<int32_t> done(ni, 0);
+    std::vector<double> obj(ni, 0.0);
+    size_t remaining = ni;
+    if (c->needs_update && max_iter > 0) {
+        st = sivf_update(c);
+        if (st != SIVF_OK) return st;
+    }
+    for (int32_t it = 0; it < max_iter && remaining > 0; ++it) {
+        st = sivf_assign(c, nullptr);
+        if (st != SIVF_OK) return st;
+        // an instance converges at its first assignment (r > 1) that changes no label;
+        // later iterations leave it untouched (every cluster invariant)
+        for (size_t m = 0; m < ni; ++m) {
+            if (!done[m] && c->iter > 1 && c->inst_changed_h[m] == 0) {
+                done[m] = c->iter;
+                --remaining;
+            }
+        }
+        if (remaining == 0) break;
+        st = sivf_update(c);
+        if (st != SIVF_OK) return st;
+        for (size_t m = 0; m < ni; ++m)
+            if (!done[m]) obj[m] = c->inst_obj_update_h[m];
+    }
+    for (size_t m = 0; m < ni; ++m) {
+        if (iters_out) iters_out[m] = done[m] ? done[m] : c->iter;
+        if (objective_out) objective_out[m] = obj[m];
+    }
+    return SIVF_OK;
+}
+
+sivf_status sivf_batch_get_labels(sivf_ctx *c, int32_t inst, int32_t *dst) {
+    if (!c) return SIVF_ERR_INVALID_ARG;
+    if (c->latched) return SIVF_ERR_STATE;
+    if (inst < 0 || inst >= c->n_inst || !dst) return fail(c, SIVF_ERR_INVALID_ARG, "bad instance or dst");
+    const int64_t b = c->inst_obj_h[(size_t)inst], n = c->inst_obj_h[(size_t)inst + 1] - b;
+    API_CUDA(c, cudaMemcpyAsync(dst, c->labels + b, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->stream), "copy");
+    API_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
+    const int32_t koff = c->inst_k_h[(size_t)inst];
+    for (int64_t i = 0; i < n; ++i)
+        if (dst[i] >= 0) dst[i] -= koff;
+    return SIVF_OK;
+}
+
+sivf_status sivf_batch_instance_stats(sivf_ctx *c, int32_t inst, int64_t *changed, double *objective_assign,
+                                      double *objective_update) {
+    if (!c) return SIVF_ERR_INVALID_ARG;
+    if (inst < 0 || inst >= c->n_inst) return fail(c, SIVF_ERR_INVALID_ARG, "bad instance");
+    if (changed) *changed = (int64_t)c->inst_changed_h[(size_t)inst];
+    if (objective_assign) *objective_assign = c->inst_obj_assign_h[(size_t)inst];
+    if (objective_update) *objective_update = c->inst_obj_update_h[(size_t)inst];
+    return SIVF_OK;
 }
 
 void sivf_destroy(sivf_ctx *c) {

@@ -59,10 +59,18 @@ struct AssignParams {
     uint32_t *own;
     const uint8_t *lam_prev;
     const int32_t *mov_list;
-    const int32_t *n_mov;
     uint8_t *moving;
     DevCounters *ctr;
     double eps, eta;
+    // instances: objects [inst_obj[m], inst_obj[m+1]) and clusters
+    // [inst_k[m], inst_k[m+1]) form instance m; moving ids of instance m are
+    // mov_list[mov_beg[m] .. mov_beg[m+1]). The scan arrays hold local ids.
+    int32_t n_inst;
+    int32_t kmax;
+    const int64_t *inst_obj;
+    const int32_t *inst_k;
+    const int32_t *mov_beg;
+    unsigned long long *inst_changed;
 };
 
 template <int PREC>
@@ -206,7 +214,7 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
     constexpr bool PACKED = CID16 && PREC != SIVF_FP32;
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int NW = T / 32;
-    const int kpad = (P.k + 3) & ~3;
+    const int kpad = (P.kmax + 3) & ~3;
     uint32_t *rho = smem;
     float *s_vs = reinterpret_cast<float *>(smem + kpad);
     int *s_start = reinterpret_cast<int *>(s_vs + T);
@@ -233,10 +241,25 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
         const int64_t i = s_obj;
         if (i >= P.N) break;
         const int64_t rb = P.row_ptr[i], re = P.row_ptr[i + 1];
-        const int32_t a_prev = P.labels_prev[i];
+        // instance of object i: largest m with inst_obj[m] <= i
+        int inst = 0;
+        {
+            int lo = 0, hi = P.n_inst - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (P.inst_obj[mid] <= i) lo = mid; else hi = mid - 1;
+            }
+            inst = lo;
+        }
+        const int k_off = P.inst_k[inst];
+        const int km = P.inst_k[inst + 1] - k_off;
+        const int32_t a_prev = P.labels_prev[i];  // global id, -1 before the first assignment
+        const int a_loc = a_prev >= 0 ? a_prev - k_off : -1;
         const uint32_t own_q = P.own[i];
         const bool filt = P.icp && a_prev >= 0 && own_q != OWN_INVALID && P.lam_prev[a_prev] != 0;
-        const int n_mov = filt ? *P.n_mov : 0;
+        const int mb = P.mov_beg[inst];
+        const int n_mov = filt ? P.mov_beg[inst + 1] - mb : 0;
+        const int32_t *movs = P.mov_list + mb;
 
         // ---- similarity scan (Algorithm 4, lines 7-13) ----
         // Work items are chunks of CH = 32 * UNR postings of one list
@@ -310,7 +333,7 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
                     float uu[UNR];
 #pragma unroll
                     for (int m = 0; m < UNR; ++m) {
-                        cc[m] = (int)__ldg(pc + 32 * m);
+                        cc[m] = (int)__ldg(pc + 32 * m) - (CID16 ? 0 : k_off);
                         uu[m] = decode_u<PREC>(__ldg(pv + 32 * m));
                     }
 #pragma unroll
@@ -321,7 +344,7 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
 #pragma unroll
                     for (int m = 0; m < UNR; ++m) {
                         if (32 * m + lane < rem) {
-                            cc[m] = (int)__ldg(pc + 32 * m);
+                            cc[m] = (int)__ldg(pc + 32 * m) - (CID16 ? 0 : k_off);
                             uu[m] = decode_u<PREC>(__ldg(pv + 32 * m));
                         }
                     }
@@ -338,14 +361,15 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
         t.bv = 0u;
         t.bi = INT32_MAX;
         t.sv = -1;
+        // candidates by local id (same order as global ids within the instance)
         if (!filt) {
-            for (int j = tid; j < P.k; j += T) top2_push(t, rho[j], j);
+            for (int j = tid; j < km; j += T) top2_push(t, rho[j], j);
         } else {
             for (int m = tid; m < n_mov; m += T) {
-                const int j = P.mov_list[m];
+                const int j = movs[m] - k_off;
                 top2_push(t, rho[j], j);
             }
-            if (tid == 0) top2_push(t, own_q, a_prev);
+            if (tid == 0) top2_push(t, own_q, a_loc);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t = top2_merge(t, top2_shfl(t, o));
@@ -378,12 +402,12 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
             double wbest = -1.0;
             int wj = INT32_MAX;
             int ncand = 0;
-            const int total = filt ? n_mov : P.k;
+            const int total = filt ? n_mov : km;
             for (int base = warp * 32; base < total; base += T) {
                 const int m = base + lane;
                 int j = -1;
                 if (m < total) {
-                    j = filt ? P.mov_list[m] : m;
+                    j = filt ? movs[m] - k_off : m;
                     if (rho[j] < thr) j = -1;
                 }
                 unsigned bal = __ballot_sync(0xffffffffu, j >= 0);
@@ -391,7 +415,7 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
                     const int src = __ffs(bal) - 1;
                     bal &= bal - 1;
                     const int jc = __shfl_sync(0xffffffffu, j, src);
-                    const double x = exact_score(P, rb, re, jc, lane);
+                    const double x = exact_score(P, rb, re, k_off + jc, lane);
                     ++ncand;
                     if (x > wbest || (x == wbest && jc < wj)) {
                         wbest = x;
@@ -402,9 +426,9 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
             if (filt && warp == 0 && own_q >= thr) {
                 const double x = exact_score(P, rb, re, a_prev, lane);
                 ++ncand;
-                if (x > wbest || (x == wbest && a_prev < wj)) {
+                if (x > wbest || (x == wbest && a_loc < wj)) {
                     wbest = x;
-                    wj = a_prev;
+                    wj = a_loc;
                 }
             }
             if (lane == 0) {
@@ -430,22 +454,24 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
 
         // ---- write the assignment, mark moving clusters (lines 17-19) ----
         if (tid == 0) {
-            const int a = s_winner;
+            const int al = s_winner;  // local id
+            const int a = k_off + al;
             P.labels[i] = a;
-            P.own[i] = (filt && a == a_prev) ? own_q : rho[a];
+            P.own[i] = (filt && al == a_loc) ? own_q : rho[al];
             if (a != a_prev) {
                 c_chg += 1;
                 P.moving[a] = 1;
                 if (a_prev >= 0) P.moving[a_prev] = 1;
+                if (P.n_inst > 1) atomicAdd(P.inst_changed + inst, 1ull);
             }
             c_filt += filt ? 1ull : 0ull;
-            c_sim += filt ? (unsigned long long)n_mov : (unsigned long long)P.k;
+            c_sim += filt ? (unsigned long long)n_mov : (unsigned long long)km;
         }
         __syncthreads();
         if (!filt) {
-            for (int j = tid; j < P.k; j += T) rho[j] = 0u;
+            for (int j = tid; j < km; j += T) rho[j] = 0u;
         } else {
-            for (int m = tid; m < n_mov; m += T) rho[P.mov_list[m]] = 0u;
+            for (int m = tid; m < n_mov; m += T) rho[movs[m] - k_off] = 0u;
         }
         __syncthreads();
     }
@@ -465,9 +491,11 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
     }
 }
 
-// lambda^[r] from the moving flags, and the ascending list of moving ids.
+// lambda^[r] from the moving flags, the ascending list of moving ids, and
+// where each instance's moving ids start in that list.
 __global__ void __launch_bounds__(1024) finalize_kernel(int32_t k, int first_iter, const uint8_t *moving,
                                                         uint8_t *lam, int32_t *mov_list, int32_t *n_mov,
+                                                        int32_t n_inst, const int32_t *inst_k, int32_t *mov_beg,
                                                         DevCounters *ctr) {
     __shared__ int warp_s[32];
     __shared__ int total;
@@ -484,6 +512,16 @@ __global__ void __launch_bounds__(1024) finalize_kernel(int32_t k, int first_ite
         carry += total;
         __syncthreads();
     }
+    // mov_beg[m] = number of moving ids below the instance's first cluster
+    for (int m = threadIdx.x; m <= n_inst; m += 1024) {
+        const int key = inst_k[m];
+        int lo = 0, hi = carry;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (mov_list[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        mov_beg[m] = lo;
+    }
     if (threadIdx.x == 0) {
         *n_mov = carry;
         ctr->n_moving = (unsigned long long)carry;
@@ -492,7 +530,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(int32_t k, int first_ite
 
 template <int T, int PREC, bool CID16>
 cudaError_t launch_t(sivf_ctx *c, const AssignParams &P, int ctas_per_sm) {
-    const int kpad = (c->k + 3) & ~3;
+    const int kpad = (c->kmax + 3) & ~3;
     const size_t smem = (size_t)kpad * 4 + (size_t)T * 16;
     auto kern = assign_kernel<T, PREC, CID16>;
     SIVF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -547,8 +585,13 @@ cudaError_t launch_assign(sivf_ctx *c) {
     P.own = c->own;
     P.lam_prev = c->lam_prev;
     P.mov_list = c->mov_list;
-    P.n_mov = c->n_mov_dev;
     P.moving = c->moving;
+    P.n_inst = c->n_inst;
+    P.kmax = c->kmax;
+    P.inst_obj = c->inst_obj;
+    P.inst_k = c->inst_k;
+    P.mov_beg = c->mov_beg;
+    P.inst_changed = c->inst_changed;
     P.ctr = c->ctr;
     if (c->cfg.prec == SIVF_BF16) {
         P.eps = 0.00390625;  // 2^-8: bf16 keeps 8 significant bits
@@ -569,7 +612,7 @@ cudaError_t launch_assign(sivf_ctx *c) {
 
 cudaError_t launch_finalize_assign(sivf_ctx *c) {
     finalize_kernel<<<1, 1024, 0, c->stream>>>(c->k, c->iter == 1 ? 1 : 0, c->moving, c->lam, c->mov_list,
-                                               c->n_mov_dev, c->ctr);
+                                               c->n_mov_dev, c->n_inst, c->inst_k, c->mov_beg, c->ctr);
     note_launch();
     return cudaGetLastError();
 }

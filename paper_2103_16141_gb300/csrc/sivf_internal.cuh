@@ -21,6 +21,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "sivf.h"
 
@@ -119,7 +120,7 @@ struct sivf_ctx {
     // counters and step scratch
     sivf::DevCounters *ctr = nullptr;
     sivf::DevCounters *ctr_host = nullptr;  // pinned mirror
-    double *obj_dev = nullptr;              // [2]: J_assign, J_update
+    double *obj_dev = nullptr;              // [2 * n_inst]: J_assign, J_update per instance
     sivf::Workspace ws;
     size_t ws_bytes = 0;
     size_t owned_bytes = 0;
@@ -127,6 +128,25 @@ struct sivf_ctx {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int assign_threads = 0, assign_ctas_per_sm = 0;
     unsigned long long launch_base = 0;  // g_launches at init / reseed
+
+    // independent instances sharing one context: objects [inst_obj[m],
+    // inst_obj[m+1]), clusters [inst_k[m], inst_k[m+1]), terms [inst_d[m],
+    // inst_d[m+1]) belong to instance m (one instance for sivf_init)
+    int32_t n_inst = 1;
+    int32_t kmax = 0;                  // largest instance k (shared-memory score vector)
+    int64_t *inst_obj = nullptr;       // device [n_inst+1]
+    int32_t *inst_k = nullptr;         // device [n_inst+1]
+    int32_t *mov_beg = nullptr;        // device [n_inst+1]
+    int32_t *clu_koff = nullptr;       // device [k]: first cluster of the cluster's instance
+    unsigned long long *inst_changed = nullptr;  // device [n_inst]
+    std::vector<int64_t> inst_obj_h;
+    std::vector<int32_t> inst_k_h, inst_d_h;
+    std::vector<unsigned long long> inst_changed_h;
+    std::vector<double> inst_obj_assign_h, inst_obj_update_h;
+    // concatenated object CSR owned by a batch context (null for sivf_init)
+    int64_t *own_row_ptr = nullptr;
+    int32_t *own_idx = nullptr;
+    float *own_val = nullptr;
 };
 
 namespace sivf {

@@ -315,11 +315,15 @@ __global__ void __launch_bounds__(WR_THREADS) k_write_rows(
     }
 }
 
-__global__ void __launch_bounds__(1024) k_sum2(int32_t k, const double *a, const double *b, double *out) {
-    // fixed-order reduction: per-thread strided partial sums, then a tree
+// Per-instance objective sums (one CTA per instance), fixed order:
+// per-thread strided partial sums, then a tree.
+__global__ void __launch_bounds__(1024) k_sum_inst(const int32_t *inst_k, const double *a, const double *b,
+                                                   double *out) {
     __shared__ double sa[1024], sb[1024];
+    const int m = blockIdx.x;
+    const int j0 = inst_k[m], j1 = inst_k[m + 1];
     double x = 0.0, y = 0.0;
-    for (int j = threadIdx.x; j < k; j += 1024) {
+    for (int j = j0 + threadIdx.x; j < j1; j += 1024) {
         x += a[j];
         y += b[j];
     }
@@ -334,8 +338,8 @@ __global__ void __launch_bounds__(1024) k_sum2(int32_t k, const double *a, const
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        out[0] = sa[0];
-        out[1] = sb[0];
+        out[2 * m] = sa[0];
+        out[2 * m + 1] = sb[0];
     }
 }
 
@@ -359,14 +363,18 @@ __global__ void k_if_lens(int32_t D, const uint32_t *cnt2, int64_t *len, int32_t
     }
 }
 
-__global__ void k_if_fill(int64_t n, const uint32_t *order, const int32_t *cclu, const float *cval, int prec,
-                          int32_t *if_cid, uint16_t *if_cid16, uint32_t *if_pack, float *if_val,
-                          uint16_t *if_lp) {
+// if_cid holds global cluster ids; the scan arrays (if_cid16, if_pack) hold
+// ids local to the cluster's instance.
+__global__ void k_if_fill(int64_t n, const uint32_t *order, const int32_t *cclu, const int32_t *clu_koff,
+                          const float *cval, int prec, int32_t *if_cid, uint16_t *if_cid16, uint32_t *if_pack,
+                          float *if_val, uint16_t *if_lp) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t e = order[q];
         const float u = cval[e];
-        if_cid[q] = cclu[e];
-        if (if_cid16) if_cid16[q] = (uint16_t)cclu[e];
+        const int32_t j = cclu[e];
+        const uint32_t jl = (uint32_t)(j - clu_koff[j]);
+        if_cid[q] = j;
+        if (if_cid16) if_cid16[q] = (uint16_t)jl;
         if_val[q] = u;
         unsigned short lp = 0;
         if (prec == SIVF_BF16) {
@@ -377,7 +385,7 @@ __global__ void k_if_fill(int64_t n, const uint32_t *order, const int32_t *cclu,
             if (lp == 0 && u > 0.0f) lp = 1;  // keep every posting strictly positive
             if_lp[q] = lp;
         }
-        if (if_pack) if_pack[q] = ((uint32_t)cclu[e] << 16) | (uint32_t)lp;
+        if (if_pack) if_pack[q] = (jl << 16) | (uint32_t)lp;
     }
 }
 
@@ -486,7 +494,7 @@ cudaError_t build_inverted_file(sivf_ctx *c) {
     bool alt = false;
     SIVF_CUDA_TRY(radix_sort_pairs(k0, v0, k1, v1, n, c->bits_t + 1, &alt, ws, c->stream));
     if (n > 0) {
-        k_if_fill<<<blocks_for(n), TPB, 0, c->stream>>>(n, alt ? v1 : v0, c->cclu, c->cval[cur], (int)c->cfg.prec,
+        k_if_fill<<<blocks_for(n), TPB, 0, c->stream>>>(n, alt ? v1 : v0, c->cclu, c->clu_koff, c->cval[cur], (int)c->cfg.prec,
                                                        c->if_cid, c->if_cid16, c->if_pack, c->if_val, c->if_lp);
         note_launch();
     }
@@ -596,7 +604,7 @@ cudaError_t run_update(sivf_ctx *c) {
         k, flag, rrank, supoff, supend, uterm, usum, cnt, c->coff[old], c->cterm[old], c->cval[old], c->snorm,
         c->coff[nw], c->cterm[nw], c->cval[nw], c->cclu, c->snorm_new, jAd, jUd);
     note_launch();
-    k_sum2<<<1, 1024, 0, s>>>(k, jAd, jUd, c->obj_dev);
+    k_sum_inst<<<(unsigned)c->n_inst, 1024, 0, s>>>(c->inst_k, jAd, jUd, c->obj_dev);
     note_launch();
     SIVF_CUDA_TRY(cudaGetLastError());
     c->cur = nw;

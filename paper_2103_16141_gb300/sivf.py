@@ -35,6 +35,11 @@ class sivf_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class sivf_instance_desc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("D", ctypes.c_int32), ("k", ctypes.c_int32), ("row_ptr", ctypes.c_void_p),
+                ("idx", ctypes.c_void_p), ("val", ctypes.c_void_p), ("init_ids", ctypes.c_void_p)]
+
+
 class SivfError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
@@ -89,6 +94,16 @@ def load(build_if_missing: bool = True):
         lib.sivf_last_error.restype = ctypes.c_char_p
         lib.sivf_destroy.argtypes = [p]
         lib.sivf_destroy.restype = None
+        lib.sivf_batch_init.argtypes = [ctypes.POINTER(p), ctypes.POINTER(sivf_config), i32,
+                                        ctypes.POINTER(sivf_instance_desc), p]
+        lib.sivf_batch_init.restype = st
+        lib.sivf_batch_run.argtypes = [p, i32, p, p]
+        lib.sivf_batch_run.restype = st
+        lib.sivf_batch_get_labels.argtypes = [p, i32, p]
+        lib.sivf_batch_get_labels.restype = st
+        lib.sivf_batch_instance_stats.argtypes = [p, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.POINTER(ctypes.c_double)]
+        lib.sivf_batch_instance_stats.restype = st
         lib.sivf_build_inverted_file_noalloc.argtypes = [i32, i32, i64, p, p, p, p, p, p, p, p, p]
         lib.sivf_build_inverted_file_noalloc.restype = st
         _lib = lib
@@ -288,3 +303,91 @@ class SIVF:
         _check(lib, self.ctx, lib.sivf_get_inverted_file(self.ctx, off.ctypes.data, mf0.ctypes.data,
                                                          cid.ctypes.data, u.ctypes.data, len(cid), ctypes.byref(n)))
         return off, mf0, cid[:n.value], u[:n.value]
+
+
+def sivf_batch_init(cfg: sivf_config, descs) -> int:
+    lib = load()
+    arr = (sivf_instance_desc * len(descs))(*descs)
+    ctx = ctypes.c_void_p()
+    _check(lib, None, lib.sivf_batch_init(ctypes.byref(ctx), ctypes.byref(cfg), len(descs), arr,
+                                          _current_stream()))
+    return ctx.value
+
+
+def _current_stream() -> int:
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class SIVFBatch:
+    """Many independent instances in one context (sivf_batch_init).
+
+    corpora: list of objects with row_ptr, idx, val (numpy or torch), D;
+    ks: clusters per instance; init_ids: per-instance local seed ids.
+    """
+
+    def __init__(self, corpora, ks, init_ids, precision: str = "fp32", icp: bool = True, threads: int = 0,
+                 ctas_per_sm: int = 0):
+        import numpy as np
+        import torch
+
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self._keep = []
+        descs = []
+        for c, k, ini in zip(corpora, ks, init_ids):
+            rp = torch.as_tensor(np.ascontiguousarray(c.row_ptr), dtype=torch.int64).to(dev)
+            ix = torch.as_tensor(np.ascontiguousarray(c.idx), dtype=torch.int32).to(dev)
+            vl = torch.as_tensor(np.ascontiguousarray(c.val), dtype=torch.float32).to(dev)
+            ii = np.ascontiguousarray(np.asarray(ini, dtype=np.int32))
+            self._keep.append((rp, ix, vl, ii))
+            descs.append(sivf_instance_desc(int(rp.numel() - 1), int(c.D), int(k), rp.data_ptr(), ix.data_ptr(),
+                                            vl.data_ptr(), ii.ctypes.data))
+        self.n_inst = len(descs)
+        self.Ns = [d.N for d in descs]
+        self.ks = [int(k) for k in ks]
+        cfg = sivf_config(PRECISIONS[precision], int(bool(icp)), int(threads), int(ctas_per_sm), 0)
+        self.ctx = sivf_batch_init(cfg, descs)
+        self._keep = None  # the library copied the corpora
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            sivf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def assign(self) -> int:
+        return sivf_assign(self.ctx)
+
+    def update(self) -> None:
+        sivf_update(self.ctx)
+
+    def run(self, max_iter: int):
+        import numpy as np
+        lib = load()
+        it = np.zeros(self.n_inst, dtype=np.int32)
+        obj = np.zeros(self.n_inst, dtype=np.float64)
+        _check(lib, self.ctx, lib.sivf_batch_run(self.ctx, max_iter, it.ctypes.data, obj.ctypes.data))
+        return it, obj
+
+    def labels(self, inst: int):
+        import numpy as np
+        lib = load()
+        out = np.empty(self.Ns[inst], dtype=np.int32)
+        _check(lib, self.ctx, lib.sivf_batch_get_labels(self.ctx, inst, out.ctypes.data))
+        return out
+
+    def instance_stats(self, inst: int) -> dict:
+        lib = load()
+        ch = ctypes.c_int64(0)
+        ja, ju = ctypes.c_double(0), ctypes.c_double(0)
+        _check(lib, self.ctx, lib.sivf_batch_instance_stats(self.ctx, inst, ctypes.byref(ch), ctypes.byref(ja),
+                                                            ctypes.byref(ju)))
+        return {"changed": ch.value, "objective_assign": ja.value, "objective_update": ju.value}
+
+    def stats(self) -> dict:
+        return sivf_get_stats(self.ctx).as_dict()

@@ -144,3 +144,69 @@ def test_full_size_c2_sampled_against_oracle():
         compare_centroids(g, o)
     finally:
         g.close()
+
+
+def _batch_corpora(n_inst, scale, seed0=0):
+    from synth import batched_instances, generate, init_ids
+    ws = batched_instances(n_inst, scale=scale)
+    cs = [generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, w.seed + seed0) for w in ws]
+    inis = [init_ids(w.N, w.k, w.init_seed) for w in ws]
+    return ws, cs, inis
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_batched_instances_match_their_own_oracles(precision):
+    """Several uneven instances in one context: at every iteration each
+    instance's labels equal its own FP64 oracle's (near ties excepted)."""
+    from paper_2103_16141_gb300 import SIVFBatch
+    ws, cs, inis = _batch_corpora(6, scale=0.05)
+    b = SIVFBatch(cs, [w.k for w in ws], inis, precision=precision)
+    ors = [Oracle(c, w.k, ini, icp=True) for w, c, ini in zip(ws, cs, inis)]
+    ous = [Oracle(c, w.k, ini, icp=False) for w, c, ini in zip(ws, cs, inis)]
+    done = [False] * len(ws)
+    try:
+        for _ in range(30):
+            b.assign()
+            for m, (o, ou) in enumerate(zip(ors, ous)):
+                if done[m]:
+                    continue
+                a = o.assign()
+                ou.assign()
+                best, second, _ = ou.scores()
+                n = compare_labels(b.labels(m), o.labels(), best, second, f"instance {m} r={a.r}")
+                assert n == 0
+                assert b.instance_stats(m)["changed"] == a.changed
+                if a.r > 1 and a.changed == 0:
+                    done[m] = True
+            if all(done):
+                break
+            b.update()
+            for m, (o, ou) in enumerate(zip(ors, ous)):
+                if done[m]:
+                    continue
+                u = o.update()
+                ou.update()
+                assert rel(b.instance_stats(m)["objective_update"], u.objective) <= OBJECTIVE_RTOL
+        assert all(done)
+    finally:
+        b.close()
+
+
+def test_batched_run_equals_separate_runs():
+    """sivf_batch_run gives every instance the labels and iteration count of
+    its own single-instance run."""
+    from paper_2103_16141_gb300 import SIVFBatch
+    ws, cs, inis = _batch_corpora(5, scale=0.04, seed0=100)
+    b = SIVFBatch(cs, [w.k for w in ws], inis, precision="fp16")
+    try:
+        iters, obj = b.run(50)
+        for m, (w, c, ini) in enumerate(zip(ws, cs, inis)):
+            g = gpu_instance(c, w.k, ini, precision="fp16")
+            try:
+                it1, _ = g.run(50)
+                assert np.array_equal(b.labels(m), g.labels())
+                assert iters[m] == it1
+            finally:
+                g.close()
+    finally:
+        b.close()
