@@ -46,12 +46,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS) + ["c4"])
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--icp", type=int, default=1)
     ap.add_argument("--max-iter", type=int, default=None)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--graph", type=int, default=1, help="1: iterations after the second run in one CUDA graph")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-iters", type=int, default=8)
@@ -235,8 +236,73 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """Batched workload: 64 independent corpora (seeds 0..63; N log-uniform in
+    [5K, 200K], D in [20K, 100K], mean nnz/doc in [30, 250], k in [16, 2000]),
+    FP16 postings, one context; a step is one sivf_batch_run to convergence
+    (cap 50) from the seeded centroids."""
+    import torch
+    from paper_2103_16141_gb300 import SIVFBatch, sivf as S
+    from synth import batched_instances
+
+    world, rank, local = dist_setup(args.gpus)
+    S.load()
+    prec = args.precision or "fp16"
+    ws = batched_instances(64, max_iter=args.max_iter or 50)
+    cs = [generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, w.seed) for w in ws]
+    inis = [init_ids(w.N, w.k, w.init_seed) for w in ws]
+    b = SIVFBatch(cs, [w.k for w in ws], inis, precision=prec, icp=bool(args.icp), threads=args.threads,
+                  ctas_per_sm=args.ctas_per_sm, use_graph=bool(args.graph))
+    gini = np.ascontiguousarray(np.concatenate([ini + off for ini, off in
+                                                zip(inis, np.cumsum([0] + [w.N for w in ws[:-1]]))]), dtype=np.int32)
+    max_iter = ws[0].max_iter
+    stream = torch.cuda.current_stream()
+
+    def one_run():
+        S.sivf_reseed(b.ctx, gini.ctypes.data)  # gini stays referenced during the call
+        its, _ = b.run(max_iter)
+        return its, b.stats()
+
+    for _ in range(args.warmup):
+        one_run()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier_and_sync(world)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    obj_iters = 0
+    launches = 0
+    for _ in range(args.steps):
+        its, st = one_run()
+        obj_iters += int(sum(w.N * int(i) for w, i in zip(ws, its)))
+        launches += st["launches"]
+    ev1.record(stream)
+    barrier_and_sync(world)
+    clocks = sampler.stop()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    value = sum_over_ranks(float(obj_iters), world) / (ms / 1e3)
+    if rank == 0:
+        nnz = sum(c.nnz for c in cs)
+        line = {"metric": "objects/s (Lloyd iterations of SIVF spherical k-means, 64 batched instances)",
+                "value": value, "unit": "objects/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": f"{prec}-postings/f32-products/fixed-point-sum", "data": "synthetic",
+                "config": {"workload": f"c4: 64 instances, N={sum(w.N for w in ws)} total, nnz={nnz}, "
+                                       f"k={sum(w.k for w in ws)} total, max k={max(w.k for w in ws)}",
+                           "iterations_per_instance": [int(i) for i in its], "max_iter": max_iter},
+                "gpu_launches": int(launches), "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    b.close()
+
+
 def main():
     args = parse()
+    if args.config == "c4":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no CPU reference arm"}))
+            return
+        run_batched(args)
+        return
     w = CONFIGS[args.config]
     if args.precision:
         w = w.scaled(precision=args.precision)
@@ -256,14 +322,14 @@ def main():
     ini = init_ids(w.N, w.k, w.init_seed)
     dev = torch.device("cuda", torch.cuda.current_device())
     g = SIVF(c.row_ptr, c.idx, c.val, c.D, w.k, ini, precision=w.precision, icp=bool(args.icp),
-             threads=args.threads, ctas_per_sm=args.ctas_per_sm)
+             threads=args.threads, ctas_per_sm=args.ctas_per_sm, use_graph=bool(args.graph))
     stream = torch.cuda.current_stream()
 
-    def one_run():
+    def one_run_stepped():
+        """Host-stepped run: per-iteration counters and per-launch device times."""
         g.reseed(ini)
         iters = 0
         per = []
-        launches_at_seed = 0
         for _ in range(w.max_iter):
             n = g.assign()
             iters += 1
@@ -273,8 +339,15 @@ def main():
                 break
             g.update()
             per[-1] = {**st, "ms_update": g.stats()["ms_update"], "centroid_nnz": g.stats()["centroid_nnz"]}
-        per[-1]["launches_run"] = g.stats()["launches"] - launches_at_seed  # reseed resets the count
+        per[-1]["launches_run"] = g.stats()["launches"]  # reseed resets the count
         return iters, per
+
+    def one_run_graph():
+        g.reseed(ini)
+        iters, _ = g.run(w.max_iter)
+        return iters, [{"launches_run": g.stats()["launches"]}]
+
+    one_run = one_run_graph if args.graph else one_run_stepped
 
     for _ in range(args.warmup):
         one_run()
@@ -298,13 +371,19 @@ def main():
     objects = sum_over_ranks(float(w.N * tot_iters), world)
     value = objects / (ms / 1e3)
 
-    # roofline of the dominant kernel (the assignment scan), live from the
-    # library's per-launch event timings over the timed region
+    # roofline of the dominant kernel (the assignment scan), from the library's
+    # per-launch event timings: over the timed region when steps are launched
+    # from the host, else over one host-stepped run of the same workload
+    kernel_times_from = "timed region"
+    if args.graph:
+        _, all_per = one_run_stepped()
+        kernel_times_from = "one host-stepped run of the same workload (graph replay hides per-launch times)"
     hbm_peak, peak_src = load_peaks()
     b_post = (B_POST16 if w.k <= 65536 else B_POST32)[w.precision]
     alg_bytes = sum(c.nnz * 8 + (w.N + 1) * 8 + p["postings"] * b_post + w.N * 16 + w.k for p in all_per)
     ms_assign = sum(p["ms_assign"] for p in all_per)
     ms_update = sum(p.get("ms_update", 0.0) for p in all_per)
+    stepped_iters = len(all_per)
     achieved = alg_bytes / (ms_assign / 1e3) / 1e9 if ms_assign > 0 else 0.0
     postings = sum(p["postings"] for p in all_per)
     iters_per_step = tot_iters / args.steps
@@ -328,7 +407,7 @@ def main():
             d_ix = ix.to(dev, non_blocking=True)
             d_vl = vl.to(dev, non_blocking=True)
             ge = SIVF(d_rp, d_ix, d_vl, c.D, w.k, ini, precision=w.precision, icp=bool(args.icp),
-                      threads=args.threads, ctas_per_sm=args.ctas_per_sm)
+                      threads=args.threads, ctas_per_sm=args.ctas_per_sm, use_graph=bool(args.graph))
             it, _ = ge.run(w.max_iter)
             e_iters += it
             S.sivf_get_labels(ge.ctx, lab_host.data_ptr(), False)
@@ -354,7 +433,8 @@ def main():
                        "precision": w.precision, "icp": bool(args.icp), "max_iter": w.max_iter,
                        "iters_per_step": iters_per_step, "sec_per_iter": ms / 1e3 / tot_iters,
                        "l2": "inputs larger than L2 (CSR 0.46 GB; inverted file > 129 MB)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "cuda_graph": bool(args.graph)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": traffic, "traffic_launch": traffic_launch,
                          "peak_source": peak_src, "kernel": "assign_kernel",
@@ -362,7 +442,8 @@ def main():
                          "note": "posting bytes are served by L2 (ncu: 94% L2 hit, DRAM bytes = traffic); "
                                  "frac > 1 means on-chip reuse, see profiles/",
                          "postings_per_s": postings / (ms_assign / 1e3) if ms_assign > 0 else None,
-                         "ms_assign_per_iter": ms_assign / tot_iters, "ms_update_per_iter": ms_update / tot_iters},
+                         "ms_assign_per_iter": ms_assign / stepped_iters, "ms_update_per_iter": ms_update / stepped_iters,
+                         "kernel_times_from": kernel_times_from},
             "gpu_launches": int(launches),
             "clocks": clocks,
         }

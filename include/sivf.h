@@ -57,6 +57,10 @@ typedef struct {
     int threads;         /* threads per CTA of the assignment kernel; 0 = automatic */
     int ctas_per_sm;     /* resident CTAs per SM of the assignment kernel; 0 = automatic */
     int64_t mem_cap_bytes; /* cap on library-owned device memory; 0 = no cap */
+    int use_graph;       /* 1: after the first two iterations, sivf_run / sivf_batch_run
+                            replay one CUDA graph whose conditional WHILE node runs the
+                            remaining iterations on the device (no per-iteration host
+                            round trip); 0: every step launched from the host */
 } sivf_config;
 
 /* Counters of the most recent assignment / update (host copy). */
@@ -77,6 +81,7 @@ typedef struct {
     double ms_assign;        /* device time of the last assignment step */
     double ms_update;        /* device time of the last update step */
     int64_t launches;        /* kernels launched by the library since sivf_init / sivf_reseed */
+    int64_t graph_iters;     /* iterations the last sivf_run / sivf_batch_run ran inside its CUDA graph */
 } sivf_stats;
 
 typedef struct sivf_ctx sivf_ctx; /* opaque, library-owned */
@@ -135,7 +140,9 @@ sivf_status sivf_update(sivf_ctx *ctx);
 
 /*
  * sivf_run — Algorithm 1 loop: assign, then update, until an assignment
- * (r > 1) changes no label or max_iter assignments have run.
+ * (r > 1) changes no label or max_iter assignments have run. With use_graph,
+ * iterations after the second run inside one CUDA graph (per-step device
+ * times in sivf_stats are then those of the last host-launched step).
  *   iters_out     : HOST out, may be NULL; assignment steps run by this call.
  *   objective_out : HOST out, may be NULL; J of the last assignment.
  */

@@ -51,10 +51,14 @@ void free_all(sivf_ctx *c) {
                     c->n_mov_dev, c->snorm, c->snorm_new, c->coff[0], c->coff[1], c->cterm[0], c->cterm[1],
                     c->cval[0], c->cval[1], c->cclu, c->if_off, c->if_mf0, c->if_cid, c->if_cid16, c->if_pack, c->if_val, c->if_lp,
                     c->ctr, c->obj_dev, c->ws.base, c->inst_obj, c->inst_k, c->mov_beg, c->clu_koff,
-                    c->inst_changed, c->own_row_ptr, c->own_idx, c->own_val};
+                    c->inst_changed, c->own_row_ptr, c->own_idx, c->own_val, c->clu_doff,
+                    c->loop_dev, c->done_dev, c->objf_dev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    if (c->ctr_host) cudaFreeHost(c->ctr_host);
+    destroy_loop_graph(c);
+    void *pins[] = {c->ctr_host, c->inst_changed_pin, c->obj_pin, c->nmov_pin, c->loop_pin, c->objf_pin};
+    for (void *p : pins)
+        if (p) cudaFreeHost(p);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
 }
@@ -170,6 +174,7 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
     INIT_CUDA(dmalloc(c, &c->inst_k, (size_t)ni + 1), "alloc");
     INIT_CUDA(dmalloc(c, &c->mov_beg, (size_t)ni + 1), "alloc");
     INIT_CUDA(dmalloc(c, &c->clu_koff, k), "alloc");
+    INIT_CUDA(dmalloc(c, &c->clu_doff, k), "alloc");
     INIT_CUDA(dmalloc(c, &c->inst_changed, ni), "alloc");
     for (int b = 0; b < 2; ++b) {
         INIT_CUDA(dmalloc(c, &c->coff[b], (size_t)k + 1), "alloc");
@@ -189,14 +194,22 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
     INIT_CUDA(dmalloc(c, &c->ctr, 1), "alloc");
     INIT_CUDA(dmalloc(c, &c->obj_dev, 2 * (size_t)ni), "alloc");
     INIT_CUDA(cudaMallocHost(reinterpret_cast<void **>(&c->ctr_host), sizeof(DevCounters)), "alloc host");
+    INIT_CUDA(cudaMallocHost(reinterpret_cast<void **>(&c->inst_changed_pin), sizeof(unsigned long long) * ni),
+              "alloc host");
+    INIT_CUDA(cudaMallocHost(reinterpret_cast<void **>(&c->obj_pin), sizeof(double) * 2 * ni), "alloc host");
+    INIT_CUDA(cudaMallocHost(reinterpret_cast<void **>(&c->nmov_pin), sizeof(int32_t)), "alloc host");
+    INIT_CUDA(cudaMallocHost(reinterpret_cast<void **>(&c->loop_pin), sizeof(int32_t) * (4 + (size_t)ni)), "alloc host");
+    INIT_CUDA(cudaMallocHost(reinterpret_cast<void **>(&c->objf_pin), sizeof(double) * ni), "alloc host");
+    INIT_CUDA(dmalloc(c, &c->loop_dev, 4), "alloc");
+    INIT_CUDA(dmalloc(c, &c->done_dev, ni), "alloc");
+    INIT_CUDA(dmalloc(c, &c->objf_dev, ni), "alloc");
     {
         // workspace: max of the update's two phases, plus primitive scratch
         const size_t n8 = (size_t)N * 8, k8 = (size_t)k * 8;
         // u1: 4 label key/value arrays (4 B x N), tuple counts/offsets (8 B x N),
-        // per-cluster arrays; u2: unique (term, sum) pairs (12 B x nnz) and
-        // per tuple 4 sort arrays, head/index/position and a piece sum (36 B)
-        size_t phase1 = 4 * (size_t)N * 4 + 2 * n8 + 10 * k8 + 12 * ((size_t)nnz + 1) + 36 * ((size_t)nnz + 1) +
-                        32 * 4096;
+        // per-cluster arrays; u2 per tuple: 4 sort arrays, term, rank, value,
+        // sorted value, 64-bit key, piece sum, unique term and sum (60 B)
+        size_t phase1 = 4 * (size_t)N * 4 + 2 * n8 + 14 * k8 + 64 * ((size_t)nnz + 1) + 32 * 4096;
         size_t phase2 = 16 * ((size_t)capc + 1) + 24 * ((size_t)D + 1) + 16 * 4096;
         size_t ws = phase1 > phase2 ? phase1 : phase2;
         size_t maxn = (size_t)(capc > N ? capc : N);
@@ -207,9 +220,18 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
     }
     for (auto &ev : c->ev) INIT_CUDA(cudaEventCreate(&ev), "event");
     {
-        std::vector<int32_t> koff((size_t)k);
-        for (int32_t m = 0; m < ni; ++m)
-            for (int32_t j = inst_k[(size_t)m]; j < inst_k[(size_t)m + 1]; ++j) koff[(size_t)j] = inst_k[(size_t)m];
+        std::vector<int32_t> koff((size_t)k), doff((size_t)k);
+        int32_t dmax = 1;
+        for (int32_t m = 0; m < ni; ++m) {
+            dmax = std::max(dmax, inst_d[(size_t)m + 1] - inst_d[(size_t)m]);
+            for (int32_t j = inst_k[(size_t)m]; j < inst_k[(size_t)m + 1]; ++j) {
+                koff[(size_t)j] = inst_k[(size_t)m];
+                doff[(size_t)j] = inst_d[(size_t)m];
+            }
+        }
+        c->bits_tl = std::max(1, bits_for((uint64_t)(dmax - 1)));
+        INIT_CUDA(cudaMemcpyAsync(c->clu_doff, doff.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, c->stream),
+                  "copy");
         INIT_CUDA(cudaMemcpyAsync(c->inst_obj, inst_obj.data(), sizeof(int64_t) * (ni + 1), cudaMemcpyHostToDevice,
                                   c->stream), "copy");
         INIT_CUDA(cudaMemcpyAsync(c->inst_k, inst_k.data(), sizeof(int32_t) * (ni + 1), cudaMemcpyHostToDevice,
@@ -395,51 +417,171 @@ sivf_status sivf_reseed(sivf_ctx *c, const int32_t *init_ids) {
     return SIVF_OK;
 }
 
-sivf_status sivf_assign(sivf_ctx *c, int64_t *n_changed) {
-    sivf_status st = check_usable(c);
-    if (st != SIVF_OK) return st;
-    // a^[r-1] <- a^[r]; lambda^[r-1] <- lambda^[r]
-    if (c->needs_update)
-        return fail(c, SIVF_ERR_STATE,
-                    "sivf_update must run between two assignments (and after sivf_set_labels)");
-    std::swap(c->labels, c->labels_prev);
-    std::swap(c->lam, c->lam_prev);
-    c->iter += 1;
-    API_CUDA(c, cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream), "memset");
-    API_CUDA(c, cudaMemsetAsync(c->moving, 0, c->k, c->stream), "memset");
-    API_CUDA(c, cudaMemsetAsync(c->inst_changed, 0, sizeof(unsigned long long) * c->n_inst, c->stream), "memset");
-    int32_t nmp = 0;
-    API_CUDA(c, cudaMemcpyAsync(&nmp, c->n_mov_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream), "copy");
-    API_CUDA(c, cudaEventRecord(c->ev[0], c->stream), "event");
-    API_CUDA(c, launch_assign(c), "assign kernel");
-    API_CUDA(c, launch_finalize_assign(c), "finalize kernel");
-    API_CUDA(c, cudaEventRecord(c->ev[1], c->stream), "event");
-    API_CUDA(c, cudaMemcpyAsync(c->ctr_host, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->stream), "copy");
-    if (c->n_inst > 1)
-        API_CUDA(c, cudaMemcpyAsync(c->inst_changed_h.data(), c->inst_changed, sizeof(unsigned long long) * c->n_inst,
-                                    cudaMemcpyDeviceToHost, c->stream), "copy");
-    API_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
-    if (c->n_inst == 1) c->inst_changed_h[0] = c->ctr_host->changed;
-    float ms = 0.f;
-    API_CUDA(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]), "elapsed");
+}  // extern "C"
+
+namespace sivf {
+
+// Stream operations of one assignment step (no host synchronisation). With
+// timing, CUDA events bracket the kernels and the counters are copied to the
+// pinned host mirrors; a graph body is captured without either.
+cudaError_t enqueue_assign(sivf_ctx *c, bool timing) {
+    cudaStream_t s = c->stream;
+    // a^[r-1] <- a^[r], lambda^[r-1] <- lambda^[r] (copies keep every buffer
+    // address fixed from one iteration to the next)
+    SIVF_CUDA_TRY(cudaMemcpyAsync(c->labels_prev, c->labels, sizeof(int32_t) * c->N, cudaMemcpyDeviceToDevice, s));
+    SIVF_CUDA_TRY(cudaMemcpyAsync(c->lam_prev, c->lam, c->k, cudaMemcpyDeviceToDevice, s));
+    SIVF_CUDA_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
+    SIVF_CUDA_TRY(cudaMemsetAsync(c->moving, 0, c->k, s));
+    SIVF_CUDA_TRY(cudaMemsetAsync(c->inst_changed, 0, sizeof(unsigned long long) * c->n_inst, s));
+    if (timing) {
+        SIVF_CUDA_TRY(cudaMemcpyAsync(c->nmov_pin, c->n_mov_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SIVF_CUDA_TRY(cudaEventRecord(c->ev[0], s));
+    }
+    SIVF_CUDA_TRY(launch_assign(c));
+    SIVF_CUDA_TRY(launch_finalize_assign(c));
+    if (timing) {
+        SIVF_CUDA_TRY(cudaEventRecord(c->ev[1], s));
+        SIVF_CUDA_TRY(cudaMemcpyAsync(c->ctr_host, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+        SIVF_CUDA_TRY(cudaMemcpyAsync(c->inst_changed_pin, c->inst_changed, sizeof(unsigned long long) * c->n_inst,
+                                      cudaMemcpyDeviceToHost, s));
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_update(sivf_ctx *c, bool timing) {
+    cudaStream_t s = c->stream;
+    if (timing) SIVF_CUDA_TRY(cudaEventRecord(c->ev[2], s));
+    SIVF_CUDA_TRY(run_update(c));
+    if (timing) {
+        SIVF_CUDA_TRY(cudaEventRecord(c->ev[3], s));
+        SIVF_CUDA_TRY(cudaMemcpyAsync(c->obj_pin, c->obj_dev, sizeof(double) * 2 * c->n_inst, cudaMemcpyDeviceToHost,
+                                      s));
+        SIVF_CUDA_TRY(cudaMemcpyAsync(c->ctr_host, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    }
+    return cudaSuccess;
+}
+
+}  // namespace sivf
+
+namespace {
+
+// Host bookkeeping after an assignment whose counters are in the pinned mirrors.
+sivf_status finish_assign(sivf_ctx *c, int64_t *n_changed, float ms) {
     const DevCounters &h = *c->ctr_host;
     if (h.error) {
         c->latched = true;
         c->err = "device-side check failed in the assignment";
         return SIVF_ERR_STATE;
     }
-    sivf_stats &s = c->stats;
-    s.iter = c->iter;
-    s.changed = (int64_t)h.changed;
-    s.n_moving = (int64_t)h.n_moving;
-    s.n_moving_prev = nmp;
-    s.filtered = (int64_t)h.filtered;
-    s.simcalc = (int64_t)h.simcalc;
-    s.postings = (int64_t)h.postings;
-    s.rescored = (int64_t)h.rescored;
-    s.rescore_cands = (int64_t)h.rescore_cands;
-    s.ms_assign = ms;
-    if (n_changed) *n_changed = s.changed;
+    for (int32_t m = 0; m < c->n_inst; ++m)
+        c->inst_changed_h[(size_t)m] = c->n_inst == 1 ? h.changed : c->inst_changed_pin[m];
+    sivf_stats &st = c->stats;
+    st.iter = c->iter;
+    st.changed = (int64_t)h.changed;
+    st.n_moving = (int64_t)h.n_moving;
+    st.n_moving_prev = *c->nmov_pin;
+    st.filtered = (int64_t)h.filtered;
+    st.simcalc = (int64_t)h.simcalc;
+    st.postings = (int64_t)h.postings;
+    st.rescored = (int64_t)h.rescored;
+    st.rescore_cands = (int64_t)h.rescore_cands;
+    if (ms >= 0.f) st.ms_assign = ms;
+    if (n_changed) *n_changed = st.changed;
+    return SIVF_OK;
+}
+
+sivf_status finish_update(sivf_ctx *c, float ms) {
+    if (c->ctr_host->error) {
+        c->latched = true;
+        c->err = "the centroids outgrew their buffers (more than 2 nnz + 1024 entries)";
+        return SIVF_ERR_OOM;
+    }
+    c->c_nnz = c->ctr_host->c_nnz;
+    c->if_nnz = c->c_nnz;
+    c->stats.moved_nnz = c->ctr_host->moved;
+    double ja = 0.0, ju = 0.0;
+    for (int32_t m = 0; m < c->n_inst; ++m) {
+        c->inst_obj_assign_h[(size_t)m] = c->obj_pin[2 * m];
+        c->inst_obj_update_h[(size_t)m] = c->obj_pin[2 * m + 1];
+        ja += c->obj_pin[2 * m];
+        ju += c->obj_pin[2 * m + 1];
+    }
+    c->stats.objective_assign = ja;
+    c->stats.objective_update = ju;
+    if (ms >= 0.f) c->stats.ms_update = ms;
+    c->stats.centroid_nnz = c->c_nnz;
+    c->needs_update = false;
+    return SIVF_OK;
+}
+
+// Runs iterations on the device until every instance has converged or c->iter
+// reaches max_total. done/objf: host arrays (n_inst), updated in place.
+// Requires c->iter >= 2 and no pending update.
+sivf_status graph_loop(sivf_ctx *c, int32_t max_total, std::vector<int32_t> &done, std::vector<double> &objf) {
+    const int32_t ni = c->n_inst;
+    if (!c->graph_exec) {
+        cudaError_t e = build_loop_graph(c);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->cfg.use_graph = 0;  // keep working with host-launched steps
+            c->err = std::string("graph capture unavailable (") + c->err + "), stepping from the host: " +
+                     cudaGetErrorString(e);
+            return SIVF_ERR_CUDA;
+        }
+    }
+    cudaStream_t s = c->stream;
+    int32_t *lp = c->loop_pin;
+    lp[0] = c->iter;
+    lp[1] = max_total;
+    lp[2] = 0;
+    lp[3] = 0;
+    for (int32_t m = 0; m < ni; ++m) {
+        lp[4 + m] = done[(size_t)m];
+        c->objf_pin[m] = objf[(size_t)m];
+    }
+    API_CUDA(c, cudaMemcpyAsync(c->loop_dev, lp, sizeof(int32_t) * 4, cudaMemcpyHostToDevice, s), "copy");
+    API_CUDA(c, cudaMemcpyAsync(c->done_dev, lp + 4, sizeof(int32_t) * ni, cudaMemcpyHostToDevice, s), "copy");
+    API_CUDA(c, cudaMemcpyAsync(c->objf_dev, c->objf_pin, sizeof(double) * ni, cudaMemcpyHostToDevice, s), "copy");
+    const int32_t iter0 = c->iter;
+    API_CUDA(c, cudaGraphLaunch(c->graph_exec, s), "graph launch");
+    API_CUDA(c, cudaMemcpyAsync(lp, c->loop_dev, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, s), "copy");
+    API_CUDA(c, cudaMemcpyAsync(lp + 4, c->done_dev, sizeof(int32_t) * ni, cudaMemcpyDeviceToHost, s), "copy");
+    API_CUDA(c, cudaMemcpyAsync(c->objf_pin, c->objf_dev, sizeof(double) * ni, cudaMemcpyDeviceToHost, s), "copy");
+    API_CUDA(c, cudaMemcpyAsync(c->nmov_pin, c->n_mov_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "copy");
+    API_CUDA(c, cudaMemcpyAsync(c->ctr_host, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s), "copy");
+    API_CUDA(c, cudaMemcpyAsync(c->inst_changed_pin, c->inst_changed, sizeof(unsigned long long) * ni,
+                                cudaMemcpyDeviceToHost, s), "copy");
+    API_CUDA(c, cudaMemcpyAsync(c->obj_pin, c->obj_dev, sizeof(double) * 2 * ni, cudaMemcpyDeviceToHost, s), "copy");
+    API_CUDA(c, cudaStreamSynchronize(s), "sync");
+    c->iter = lp[0];
+    for (int32_t m = 0; m < ni; ++m) {
+        done[(size_t)m] = lp[4 + m];
+        objf[(size_t)m] = c->objf_pin[m];
+    }
+    __atomic_fetch_add(&g_launches, c->launches_per_iter * (unsigned long long)(c->iter - iter0), __ATOMIC_RELAXED);
+    c->stats.graph_iters += c->iter - iter0;
+    sivf_status st = finish_assign(c, nullptr, -1.f);
+    if (st != SIVF_OK) return st;
+    return finish_update(c, -1.f);  // the body ends with an update
+}
+
+}  // namespace
+
+extern "C" {
+
+sivf_status sivf_assign(sivf_ctx *c, int64_t *n_changed) {
+    sivf_status st = check_usable(c);
+    if (st != SIVF_OK) return st;
+    if (c->needs_update)
+        return fail(c, SIVF_ERR_STATE,
+                    "sivf_update must run between two assignments (and after sivf_set_labels)");
+    c->iter += 1;
+    API_CUDA(c, enqueue_assign(c, true), "assignment");
+    API_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
+    float ms = 0.f;
+    API_CUDA(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]), "elapsed");
+    st = finish_assign(c, n_changed, ms);
+    if (st != SIVF_OK) return st;
     // the inverted file still has the lambda^[r-1] layout: the next
     // assignment needs the update that rebuilds it with lambda^[r]
     c->needs_update = true;
@@ -450,27 +592,49 @@ sivf_status sivf_update(sivf_ctx *c) {
     sivf_status st = check_usable(c);
     if (st != SIVF_OK) return st;
     if (c->iter < 1) return fail(c, SIVF_ERR_STATE, "sivf_update needs an assignment (or sivf_set_labels) first");
-    API_CUDA(c, cudaEventRecord(c->ev[2], c->stream), "event");
-    API_CUDA(c, run_update(c), "update");
-    API_CUDA(c, cudaEventRecord(c->ev[3], c->stream), "event");
-    std::vector<double> obj(2 * (size_t)c->n_inst, 0.0);
-    API_CUDA(c, cudaMemcpyAsync(obj.data(), c->obj_dev, sizeof(double) * obj.size(), cudaMemcpyDeviceToHost,
-                                c->stream), "copy");
+    API_CUDA(c, enqueue_update(c, true), "update");
     API_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
     float ms = 0.f;
     API_CUDA(c, cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]), "elapsed");
-    double ja = 0.0, ju = 0.0;
-    for (int32_t m = 0; m < c->n_inst; ++m) {
-        c->inst_obj_assign_h[(size_t)m] = obj[2 * (size_t)m];
-        c->inst_obj_update_h[(size_t)m] = obj[2 * (size_t)m + 1];
-        ja += obj[2 * (size_t)m];
-        ju += obj[2 * (size_t)m + 1];
+    return finish_update(c, ms);
+}
+
+// Shared by sivf_run and sivf_batch_run: iterate until every instance has
+// converged or max_iter assignments ran in this call. done[m] = iteration of
+// convergence (0 = not converged), objf[m] = objective at the last update.
+static sivf_status run_loop(sivf_ctx *c, int32_t max_iter, std::vector<int32_t> &done, std::vector<double> &objf) {
+    sivf_status st;
+    const size_t ni = (size_t)c->n_inst;
+    const int32_t max_total = c->iter + max_iter;
+    c->stats.graph_iters = 0;
+    size_t remaining = 0;
+    for (size_t m = 0; m < ni; ++m) remaining += done[m] == 0;
+    if (c->needs_update && max_iter > 0) {
+        st = sivf_update(c);
+        if (st != SIVF_OK) return st;
     }
-    c->stats.objective_assign = ja;
-    c->stats.objective_update = ju;
-    c->stats.ms_update = ms;
-    c->stats.centroid_nnz = c->c_nnz;
-    c->needs_update = false;
+    while (c->iter < max_total && remaining > 0) {
+        if (c->cfg.use_graph && c->iter >= 2 && !c->needs_update) {
+            st = graph_loop(c, max_total, done, objf);
+            if (st == SIVF_OK) break;
+            if (c->latched) return st;  // a real failure; otherwise fall back to host-launched steps
+        }
+        st = sivf_assign(c, nullptr);
+        if (st != SIVF_OK) return st;
+        // an instance converges at its first assignment (r > 1) that changes no
+        // label; later iterations leave it untouched (every cluster invariant)
+        for (size_t m = 0; m < ni; ++m) {
+            if (!done[m] && c->iter > 1 && c->inst_changed_h[m] == 0) {
+                done[m] = c->iter;
+                --remaining;
+            }
+        }
+        if (remaining == 0) break;
+        st = sivf_update(c);
+        if (st != SIVF_OK) return st;
+        for (size_t m = 0; m < ni; ++m)
+            if (!done[m]) objf[m] = c->inst_obj_update_h[m];
+    }
     return SIVF_OK;
 }
 
@@ -478,24 +642,13 @@ sivf_status sivf_run(sivf_ctx *c, int32_t max_iter, int32_t *iters_out, double *
     sivf_status st = check_usable(c);
     if (st != SIVF_OK) return st;
     if (max_iter < 0) return fail(c, SIVF_ERR_INVALID_ARG, "max_iter < 0");
-    int32_t done = 0;
-    double obj = 0.0;
-    if (c->needs_update && max_iter > 0) {
-        st = sivf_update(c);
-        if (st != SIVF_OK) return st;
-    }
-    for (int32_t it = 0; it < max_iter; ++it) {
-        int64_t changed = 0;
-        st = sivf_assign(c, &changed);
-        if (st != SIVF_OK) return st;
-        ++done;
-        if (c->iter > 1 && changed == 0) break;
-        st = sivf_update(c);
-        if (st != SIVF_OK) return st;
-        obj = c->stats.objective_update;
-    }
-    if (iters_out) *iters_out = done;
-    if (objective_out) *objective_out = obj;
+    const int32_t iter0 = c->iter;
+    std::vector<int32_t> done((size_t)c->n_inst, 0);
+    std::vector<double> objf((size_t)c->n_inst, 0.0);
+    st = run_loop(c, max_iter, done, objf);
+    if (st != SIVF_OK) return st;
+    if (iters_out) *iters_out = c->n_inst == 1 && done[0] ? done[0] - iter0 : c->iter - iter0;
+    if (objective_out) *objective_out = c->n_inst == 1 ? objf[0] : c->stats.objective_update;
     return SIVF_OK;
 }
 
@@ -596,32 +749,12 @@ sivf_status sivf_batch_run(sivf_ctx *c, int32_t max_iter, int32_t *iters_out, do
     if (max_iter < 0) return fail(c, SIVF_ERR_INVALID_ARG, "max_iter < 0");
     const size_t ni = (size_t)c->n_inst;
     std::vector<int32_t> done(ni, 0);
-    std::vector<double> obj(ni, 0.0);
-    size_t remaining = ni;
-    if (c->needs_update && max_iter > 0) {
-        st = sivf_update(c);
-        if (st != SIVF_OK) return st;
-    }
-    for (int32_t it = 0; it < max_iter && remaining > 0; ++it) {
-        st = sivf_assign(c, nullptr);
-        if (st != SIVF_OK) return st;
-        // an instance converges at its first assignment (r > 1) that changes no label;
-        // later iterations leave it untouched (every cluster invariant)
-        for (size_t m = 0; m < ni; ++m) {
-            if (!done[m] && c->iter > 1 && c->inst_changed_h[m] == 0) {
-                done[m] = c->iter;
-                --remaining;
-            }
-        }
-        if (remaining == 0) break;
-        st = sivf_update(c);
-        if (st != SIVF_OK) return st;
-        for (size_t m = 0; m < ni; ++m)
-            if (!done[m]) obj[m] = c->inst_obj_update_h[m];
-    }
+    std::vector<double> objf(ni, 0.0);
+    st = run_loop(c, max_iter, done, objf);
+    if (st != SIVF_OK) return st;
     for (size_t m = 0; m < ni; ++m) {
         if (iters_out) iters_out[m] = done[m] ? done[m] : c->iter;
-        if (objective_out) objective_out[m] = obj[m];
+        if (objective_out) objective_out[m] = objf[m];
     }
     return SIVF_OK;
 }

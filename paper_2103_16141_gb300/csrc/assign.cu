@@ -533,13 +533,17 @@ cudaError_t launch_t(sivf_ctx *c, const AssignParams &P, int ctas_per_sm) {
     const int kpad = (c->kmax + 3) & ~3;
     const size_t smem = (size_t)kpad * 4 + (size_t)T * 16;
     auto kern = assign_kernel<T, PREC, CID16>;
-    SIVF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int occ = 0;
-    SIVF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, smem));
-    if (occ < 1) return cudaErrorInvalidConfiguration;
-    int per_sm = ctas_per_sm > 0 ? min(ctas_per_sm, occ) : occ;
-    const int64_t grid64 = min((int64_t)c->num_sms * per_sm, c->N);
-    kern<<<(unsigned)grid64, T, smem, c->stream>>>(P);
+    // the attribute and occupancy queries are host calls that a stream capture
+    // refuses: they run on the first (host-launched) step and are cached
+    if (c->assign_grid <= 0) {
+        SIVF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int occ = 0;
+        SIVF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, smem));
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+        int per_sm = ctas_per_sm > 0 ? min(ctas_per_sm, occ) : occ;
+        c->assign_grid = min((int64_t)c->num_sms * per_sm, c->N);
+    }
+    kern<<<(unsigned)c->assign_grid, T, smem, c->stream>>>(P);
     note_launch();
     return cudaGetLastError();
 }

@@ -55,9 +55,11 @@ __device__ T block_exclusive_scan(T x, T *smem_warp, T *block_total) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SCAN_THREADS) scan_tile_sums(const T *in, int64_t n, T *tile_sums) {
+__global__ void __launch_bounds__(SCAN_THREADS) scan_tile_sums(const T *in, int64_t n, const int64_t *n_dev,
+                                                               T *tile_sums) {
     __shared__ T warp_s[32];
     __shared__ T total;
+    if (n_dev) n = min(*n_dev, n);  // never past the launch bound
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     T s = 0;
 #pragma unroll
@@ -84,9 +86,11 @@ __global__ void __launch_bounds__(1024) scan_single_block(T *data, int64_t n, T 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SCAN_THREADS) scan_tiles(const T *in, T *out, int64_t n, const T *tile_offs) {
+__global__ void __launch_bounds__(SCAN_THREADS) scan_tiles(const T *in, T *out, int64_t n, const int64_t *n_dev,
+                                                           const T *tile_offs) {
     __shared__ T warp_s[32];
     __shared__ T total;
+    if (n_dev) n = min(*n_dev, n);  // never past the launch bound
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     T v[SCAN_ITEMS];
     T s = 0;
@@ -103,8 +107,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_tiles(const T *in, T *out, 
     }
 }
 
+// n: element count, or its upper bound when n_dev (device count) is given.
 template <typename T>
-cudaError_t scan_exclusive_impl(const T *in, T *out, int64_t n, T *total, Workspace &ws, cudaStream_t s) {
+cudaError_t scan_exclusive_impl(const T *in, T *out, int64_t n, T *total, Workspace &ws, cudaStream_t s,
+                                const int64_t *n_dev = nullptr) {
     if (n <= 0) {
         if (total) SIVF_CUDA_TRY(cudaMemsetAsync(total, 0, sizeof(T), s));
         return cudaSuccess;
@@ -113,9 +119,9 @@ cudaError_t scan_exclusive_impl(const T *in, T *out, int64_t n, T *total, Worksp
     size_t mark = ws.used;
     T *sums = ws.take<T>((size_t)tiles);
     if (!sums) return cudaErrorMemoryAllocation;
-    scan_tile_sums<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, sums);
+    scan_tile_sums<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, n_dev, sums);
     scan_single_block<T><<<1, 1024, 0, s>>>(sums, tiles, total);
-    scan_tiles<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, sums);
+    scan_tiles<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, n_dev, sums);
     note_launch(3);
     ws.used = mark;
     return cudaGetLastError();
@@ -129,11 +135,12 @@ constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 4096
 constexpr int RS_MAX_BITS = 10;                 // digit width of one pass (<= 1024 buckets)
 
 template <int BITS>
-__global__ void __launch_bounds__(RS_THREADS) radix_hist(const uint32_t *keys, int64_t n, int shift,
-                                                         uint32_t *counts, int64_t tiles) {
+__global__ void __launch_bounds__(RS_THREADS) radix_hist(const uint32_t *keys, int64_t n, const int64_t *n_dev,
+                                                         int shift, uint32_t *counts, int64_t tiles) {
     constexpr int R = 1 << BITS;
     constexpr uint32_t mask = R - 1;
     __shared__ uint32_t h[R];
+    if (n_dev) n = min(*n_dev, n);  // never past the launch bound
     for (int d = threadIdx.x; d < R; d += RS_THREADS) h[d] = 0;
     __syncthreads();
     int64_t base = (int64_t)blockIdx.x * RS_TILE;
@@ -149,12 +156,14 @@ template <int BITS>
 __global__ void __launch_bounds__(RS_THREADS) radix_scatter(const uint32_t *__restrict__ kin,
                                                             const uint32_t *__restrict__ vin,
                                                             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
-                                                            int64_t n, int shift,
+                                                            int64_t n, const int64_t *__restrict__ n_dev, int shift,
                                                             const uint32_t *__restrict__ offs, int64_t tiles) {
     constexpr int R = 1 << BITS;
     constexpr uint32_t mask = R - 1;
     __shared__ uint32_t wcnt[RS_WARPS][R];
     __shared__ uint32_t toff[R];
+    if (n_dev) n = min(*n_dev, n);  // never past the launch bound
+    if ((int64_t)blockIdx.x * RS_TILE >= n) return;  // tile past the live count (block-uniform)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < R; d += RS_THREADS) {
 #pragma unroll
@@ -204,15 +213,15 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter(const uint32_t *__re
 }
 
 template <int BITS>
-void radix_pass(const uint32_t *ka, const uint32_t *va, uint32_t *kb, uint32_t *vb, int64_t n, int shift,
-                uint32_t *counts, int64_t tiles, Workspace &ws, cudaStream_t s, cudaError_t *err) {
-    radix_hist<BITS><<<(unsigned)tiles, RS_THREADS, 0, s>>>(ka, n, shift, counts, tiles);
+void radix_pass(const uint32_t *ka, const uint32_t *va, uint32_t *kb, uint32_t *vb, int64_t n, const int64_t *n_dev,
+                int shift, uint32_t *counts, int64_t tiles, Workspace &ws, cudaStream_t s, cudaError_t *err) {
+    radix_hist<BITS><<<(unsigned)tiles, RS_THREADS, 0, s>>>(ka, n, n_dev, shift, counts, tiles);
     cudaError_t e = scan_exclusive_impl<uint32_t>(counts, counts, tiles * (1 << BITS), nullptr, ws, s);
     if (e != cudaSuccess) {
         *err = e;
         return;
     }
-    radix_scatter<BITS><<<(unsigned)tiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, counts, tiles);
+    radix_scatter<BITS><<<(unsigned)tiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, n_dev, shift, counts, tiles);
     note_launch(2);
 }
 
@@ -227,10 +236,20 @@ cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, Wor
     return scan_exclusive_impl<uint32_t>(in, out, n, nullptr, ws, s);
 }
 
+cudaError_t scan_exclusive_u32_dev(const uint32_t *in, uint32_t *out, int64_t nmax, const int64_t *n_dev,
+                                   uint32_t *total, Workspace &ws, cudaStream_t s) {
+    return scan_exclusive_impl<uint32_t>(in, out, nmax, total, ws, s, n_dev);
+}
+
 cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, int64_t n, int nbits,
                              bool *result_in_alt, Workspace &ws, cudaStream_t s) {
+    return radix_sort_pairs_dev(k0, v0, k1, v1, n, nullptr, nbits, result_in_alt, ws, s);
+}
+
+cudaError_t radix_sort_pairs_dev(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, int64_t n,
+                                 const int64_t *n_dev, int nbits, bool *result_in_alt, Workspace &ws, cudaStream_t s) {
     *result_in_alt = false;
-    if (n <= 1 || nbits <= 0) return cudaSuccess;
+    if (n <= 0 || nbits <= 0 || (n == 1 && !n_dev)) return cudaSuccess;
     if (n > (int64_t)0xFFFFFFFFll || nbits > 32) return cudaErrorInvalidValue;
     // fewest passes of at most RS_MAX_BITS bits, widths as equal as possible
     const int passes = (nbits + RS_MAX_BITS - 1) / RS_MAX_BITS;
@@ -243,16 +262,16 @@ cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t 
     cudaError_t err = cudaSuccess;
     for (int shift = 0; shift < nbits; shift += width) {
         switch (width) {
-            case 1: radix_pass<1>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
-            case 2: radix_pass<2>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
-            case 3: radix_pass<3>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
-            case 4: radix_pass<4>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
-            case 5: radix_pass<5>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
-            case 6: radix_pass<6>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
-            case 7: radix_pass<7>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
-            case 8: radix_pass<8>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
-            case 9: radix_pass<9>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
-            default: radix_pass<10>(ka, va, kb, vb, n, shift, counts, tiles, ws, s, &err); break;
+            case 1: radix_pass<1>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
+            case 2: radix_pass<2>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
+            case 3: radix_pass<3>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
+            case 4: radix_pass<4>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
+            case 5: radix_pass<5>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
+            case 6: radix_pass<6>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
+            case 7: radix_pass<7>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
+            case 8: radix_pass<8>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
+            case 9: radix_pass<9>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
+            default: radix_pass<10>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
         }
         if (err != cudaSuccess) return err;
         uint32_t *t = ka; ka = kb; kb = t;

@@ -50,7 +50,9 @@ struct DevCounters {
     unsigned long long n_moving;     // lambda^[r] = 0 count (written by finalize)
     unsigned long long work;         // object work counter of the assignment kernel
     unsigned long long error;        // nonzero: device-side check failed (code)
-    unsigned long long pad[7];
+    long long moved;                 // object non-zeros gathered by the last update
+    long long c_nnz;                 // centroid non-zeros after the last update
+    unsigned long long pad[5];
 };
 
 // Bump allocator over one device block (scratch that lives for one step).
@@ -127,6 +129,7 @@ struct sivf_ctx {
     sivf_stats stats{};
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int assign_threads = 0, assign_ctas_per_sm = 0;
+    int64_t assign_grid = 0;  // cached launch grid of the assignment kernel (0 = not yet chosen)
     unsigned long long launch_base = 0;  // g_launches at init / reseed
 
     // independent instances sharing one context: objects [inst_obj[m],
@@ -138,11 +141,26 @@ struct sivf_ctx {
     int32_t *inst_k = nullptr;         // device [n_inst+1]
     int32_t *mov_beg = nullptr;        // device [n_inst+1]
     int32_t *clu_koff = nullptr;       // device [k]: first cluster of the cluster's instance
+    int32_t *clu_doff = nullptr;       // device [k]: first term of the cluster's instance
+    int bits_tl = 0;                   // bits of an instance-local term id
     unsigned long long *inst_changed = nullptr;  // device [n_inst]
     std::vector<int64_t> inst_obj_h;
     std::vector<int32_t> inst_k_h, inst_d_h;
     std::vector<unsigned long long> inst_changed_h;
     std::vector<double> inst_obj_assign_h, inst_obj_update_h;
+    // pinned host mirrors (read after a stream synchronisation)
+    unsigned long long *inst_changed_pin = nullptr;  // [n_inst]
+    double *obj_pin = nullptr;                      // [2 * n_inst]
+    int32_t *nmov_pin = nullptr;                    // [1] moving count before the assignment
+    // device-side Lloyd loop (use_graph): WHILE conditional node around one iteration
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int32_t *loop_dev = nullptr;      // [4]: iter, max_iter, remaining, pad
+    int32_t *done_dev = nullptr;      // [n_inst]: iteration of convergence (0 = not yet)
+    double *objf_dev = nullptr;       // [n_inst]: objective at the instance's last update
+    int32_t *loop_pin = nullptr;      // pinned [4 + n_inst] mirror of loop_dev and done_dev
+    double *objf_pin = nullptr;       // pinned [n_inst]
+    unsigned long long launches_per_iter = 0;
     // concatenated object CSR owned by a batch context (null for sivf_init)
     int64_t *own_row_ptr = nullptr;
     int32_t *own_idx = nullptr;
@@ -165,11 +183,25 @@ cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, Wor
 // *result_in_alt, whether the sorted output ended in (k1, v1).
 cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, int64_t n, int nbits,
                              bool *result_in_alt, Workspace &ws, cudaStream_t s);
+// Same with the live element count in device memory (n = its upper bound):
+// no host synchronisation, so it can be captured in a CUDA graph.
+cudaError_t radix_sort_pairs_dev(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, int64_t n,
+                                 const int64_t *n_dev, int nbits, bool *result_in_alt, Workspace &ws, cudaStream_t s);
+cudaError_t scan_exclusive_u32_dev(const uint32_t *in, uint32_t *out, int64_t nmax, const int64_t *n_dev,
+                                   uint32_t *total, Workspace &ws, cudaStream_t s);
 int bits_for(uint64_t max_value);  // number of bits to hold values in [0, max_value]
 
 // ---- assign.cu ----
 cudaError_t launch_assign(sivf_ctx *c);
 cudaError_t launch_finalize_assign(sivf_ctx *c);
+
+// ---- graph.cu ----
+cudaError_t build_loop_graph(sivf_ctx *c);
+void destroy_loop_graph(sivf_ctx *c);
+
+// ---- api.cu (step enqueue without host synchronisation) ----
+cudaError_t enqueue_assign(sivf_ctx *c, bool timing);
+cudaError_t enqueue_update(sivf_ctx *c, bool timing);
 
 // ---- update.cu ----
 cudaError_t run_update(sivf_ctx *c);

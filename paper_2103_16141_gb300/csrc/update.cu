@@ -142,45 +142,114 @@ __global__ void k_recompute_flags(int32_t k, const uint8_t *lam, const int64_t *
 // ---------------- u2: cluster sums ----------------
 
 __global__ void k_member_tuples(int64_t N, const uint32_t *perm, const int32_t *labels, const int64_t *flag,
-                                const int64_t *rrank, int64_t r0, int64_t r1, const int64_t *row_ptr,
-                                int64_t *tc) {
+                                const int64_t *row_ptr, int64_t *tc) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = perm[p];
-        const int32_t j = labels[i];
-        int64_t n = 0;
-        if (flag[j]) {
-            const int64_t r = rrank[j];
-            if (r >= r0 && r < r1) n = row_ptr[i + 1] - row_ptr[i];
-        }
-        tc[p] = n;
+        tc[p] = flag[labels[i]] ? row_ptr[i + 1] - row_ptr[i] : 0;
     }
 }
 
+// One warp per member (in cluster, then object order): its (term, value)
+// pairs become tuples t = toff[p] + h with the cluster's rank.
 __global__ void k_expand(int64_t N, const uint32_t *perm, const int32_t *labels, const int64_t *rrank,
-                         int64_t r0, const int64_t *tc, const int64_t *toff, const int64_t *row_ptr,
-                         const int32_t *idx, const float *val, int bits_t, uint32_t *keys, uint32_t *vals) {
+                         const int64_t *tc, const int64_t *toff, const int64_t *row_ptr, const int32_t *idx,
+                         const float *val, uint32_t *kterm, uint32_t *vtup, uint32_t *tterm, float *tval,
+                         uint32_t *trank) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t p = wid; p < N; p += nw) {
         if (tc[p] == 0) continue;
         const int64_t i = perm[p];
-        const uint32_t rk = (uint32_t)(rrank[labels[i]] - r0);
+        const uint32_t rk = (uint32_t)rrank[labels[i]];
         const int64_t b = row_ptr[i], e = row_ptr[i + 1], o = toff[p];
         for (int64_t h = b + lane; h < e; h += 32) {
-            keys[o + (h - b)] = (rk << bits_t) | (uint32_t)idx[h];
-            vals[o + (h - b)] = __float_as_uint(val[h]);
+            const uint32_t t = (uint32_t)(o + (h - b));
+            kterm[t] = (uint32_t)idx[h];
+            vtup[t] = t;
+            tterm[t] = (uint32_t)idx[h];
+            tval[t] = val[h];
+            trank[t] = rk;
         }
     }
 }
 
-__global__ void k_heads(int64_t n, const uint32_t *keys, uint32_t *head) {
+// One 32-bit key per tuple when it fits: (cluster rank, instance-local term),
+// with the value's bits as the payload.
+__global__ void k_expand_packed(int64_t N, const uint32_t *perm, const int32_t *labels, const int64_t *rrank,
+                                const int64_t *tc, const int64_t *toff, const int64_t *row_ptr, const int32_t *idx,
+                                const float *val, const int32_t *clu_doff, int bits_tl, uint32_t *key,
+                                uint32_t *vbits) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = wid; p < N; p += nw) {
+        if (tc[p] == 0) continue;
+        const int64_t i = perm[p];
+        const int32_t j = labels[i];
+        const uint32_t hi = (uint32_t)rrank[j] << bits_tl;
+        const int32_t doff = clu_doff[j];
+        const int64_t b = row_ptr[i], e = row_ptr[i + 1], o = toff[p];
+        for (int64_t h = b + lane; h < e; h += 32) {
+            key[o + (h - b)] = hi | (uint32_t)(idx[h] - doff);
+            vbits[o + (h - b)] = __float_as_uint(val[h]);
+        }
+    }
+}
+
+// packed keys back to (rank << 32 | global term) and float values
+__global__ void k_unpack(int64_t nmax, const int64_t *n_dev, const uint32_t *key, const uint32_t *vbits,
+                         int bits_tl, const int32_t *rank2clu, const int32_t *clu_doff, unsigned long long *key64,
+                         float *sval) {
+    const int64_t n = *n_dev;
+    const uint32_t tmask = (1u << bits_tl) - 1u;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t kk = key[q];
+        const uint32_t r = kk >> bits_tl;
+        const uint32_t t = (kk & tmask) + (uint32_t)clu_doff[rank2clu[r]];
+        key64[q] = ((unsigned long long)r << 32) | (unsigned long long)t;
+        sval[q] = __uint_as_float(vbits[q]);
+    }
+}
+
+// cluster of each rank (inverse of rrank on the recomputed clusters)
+__global__ void k_rank2clu(int32_t k, const int64_t *flag, const int64_t *rrank, int32_t *rank2clu) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < k && flag[j]) rank2clu[rrank[j]] = j;
+}
+
+// after the stable sort by term: rank keys for the stable sort by rank
+__global__ void k_rank_keys(int64_t nmax, const int64_t *n_dev, const uint32_t *vtup_sorted, const uint32_t *trank,
+                            uint32_t *krank, uint32_t *vrank) {
+    const int64_t n = *n_dev;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = vtup_sorted[q];
+        krank[q] = trank[t];
+        vrank[q] = t;
+    }
+}
+
+// tuples in (rank, term, object) order: composite key and value
+__global__ void k_compose(int64_t nmax, const int64_t *n_dev, const uint32_t *krank, const uint32_t *vtup,
+                          const uint32_t *tterm, const float *tval, unsigned long long *key64, float *sval) {
+    const int64_t n = *n_dev;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = vtup[q];
+        key64[q] = ((unsigned long long)krank[q] << 32) | (unsigned long long)tterm[t];
+        sval[q] = tval[t];
+    }
+}
+
+__global__ void k_heads(int64_t nmax, const int64_t *n_dev, const unsigned long long *key, uint32_t *head) {
+    const int64_t n = *n_dev;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        head[e] = (e == 0 || keys[e] != keys[e - 1]) ? 1u : 0u;
+        head[e] = (e == 0 || key[e] != key[e - 1]) ? 1u : 0u;
 }
 
 // position of each run of equal keys: hpos[u] = first element of run u
-__global__ void k_head_pos(int64_t n, const uint32_t *head, const uint32_t *uidx, uint32_t *hpos) {
+__global__ void k_head_pos(int64_t nmax, const int64_t *n_dev, const uint32_t *head, const uint32_t *uidx,
+                           uint32_t *hpos) {
+    const int64_t n = *n_dev;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
         if (head[e]) hpos[uidx[e]] = (uint32_t)e;
 }
@@ -191,16 +260,18 @@ __global__ void k_head_pos(int64_t n, const uint32_t *head, const uint32_t *uidx
 //     inclusive scan over the lanes, the sum of every run piece inside those
 //     32 elements, stored at the piece's last element;
 //  2. one thread per run adds its pieces in ascending position.
-__global__ void k_seg_pieces(int64_t n, const uint32_t *keys, const uint32_t *vals, double *part) {
+__global__ void k_seg_pieces(int64_t nmax, const int64_t *n_dev, const unsigned long long *keys, const float *vals,
+                             double *part) {
+    const int64_t n = *n_dev;
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t base = wid * 32; base < n; base += nw * 32) {
         const int64_t e = base + lane;
         const bool valid = e < n;
-        const uint32_t key = valid ? keys[e] : 0xFFFFFFFFu;
-        double x = valid ? (double)__uint_as_float(vals[e]) : 0.0;
-        const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+        const unsigned long long key = valid ? keys[e] : ~0ull;
+        double x = valid ? (double)vals[e] : 0.0;
+        const unsigned long long prev = __shfl_up_sync(0xffffffffu, key, 1);
         bool flag = lane == 0 || prev != key;  // a piece starts here
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -209,7 +280,7 @@ __global__ void k_seg_pieces(int64_t n, const uint32_t *keys, const uint32_t *va
             if (lane >= o && !flag) x = y + x;
             if (lane >= o) flag = flag || f;
         }
-        const uint32_t next = __shfl_down_sync(0xffffffffu, key, 1);
+        const unsigned long long next = __shfl_down_sync(0xffffffffu, key, 1);
         const bool last = valid && (lane == 31 || e == n - 1 || next != key);
         if (last) part[e] = x;
     }
@@ -217,10 +288,11 @@ __global__ void k_seg_pieces(int64_t n, const uint32_t *keys, const uint32_t *va
 
 // Runs arrive sorted by (cluster rank, term): the first and the last run of
 // each cluster record where its unique entries begin and end (no atomics).
-__global__ void k_seg_runs(int64_t n, int64_t U, const uint32_t *keys, const uint32_t *hpos, const double *part,
-                           int64_t ubase, int bits_t, int64_t r0, int32_t *uterm, double *usum, int64_t *ubeg,
-                           int64_t *uend) {
-    const uint32_t tmask = (1u << bits_t) - 1u;
+__global__ void k_seg_runs(int64_t nmax, const int64_t *n_dev, const uint32_t *U_dev,
+                           const unsigned long long *keys, const uint32_t *hpos, const double *part, int32_t *uterm,
+                           double *usum, int64_t *ubeg, int64_t *uend) {
+    const int64_t n = *n_dev;
+    const int64_t U = n > 0 ? (int64_t)*U_dev : 0;
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U; u += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = hpos[u];
         const int64_t e = (u + 1 < U) ? (int64_t)hpos[u + 1] : n;
@@ -229,12 +301,12 @@ __global__ void k_seg_runs(int64_t n, int64_t U, const uint32_t *keys, const uin
             const int64_t end = ((c + 1) << 5) < e ? ((c + 1) << 5) : e;
             acc += part[end - 1];
         }
-        const uint32_t key = keys[b];
-        const uint32_t r = key >> bits_t;
-        uterm[ubase + u] = (int32_t)(key & tmask);
-        usum[ubase + u] = acc;
-        if (u == 0 || (keys[hpos[u - 1]] >> bits_t) != r) ubeg[r0 + r] = ubase + u;
-        if (u + 1 == U || (keys[e] >> bits_t) != r) uend[r0 + r] = ubase + u + 1;
+        const unsigned long long key = keys[b];
+        const uint32_t r = (uint32_t)(key >> 32);
+        uterm[u] = (int32_t)(key & 0xFFFFFFFFull);
+        usum[u] = acc;
+        if (u == 0 || (uint32_t)(keys[hpos[u - 1]] >> 32) != r) ubeg[r] = u;
+        if (u + 1 == U || (uint32_t)(keys[e] >> 32) != r) uend[r] = u + 1;
     }
 }
 
@@ -268,12 +340,16 @@ __global__ void __launch_bounds__(WR_THREADS) k_write_rows(
     int32_t k, const int64_t *flag, const int64_t *rrank, const int64_t *supoff, const int64_t *supend,
     const int32_t *uterm, const double *usum, const int64_t *cnt, const int64_t *coff_old, const int32_t *cterm_old,
     const float *cval_old, const double *snorm_old, const int64_t *coff_new, int32_t *cterm_new, float *cval_new,
-    int32_t *cclu_new, double *snorm_new, double *jA, double *jU) {
+    int32_t *cclu_new, double *snorm_new, double *jA, double *jU, int64_t cap, unsigned long long *error) {
     __shared__ double sh[WR_THREADS];
     const int j = blockIdx.x;
     if (j >= k) return;
     const int64_t o = coff_new[j];
     const int64_t cb = coff_old[j], ce = coff_old[j + 1];
+    if (coff_new[k] > cap) {  // more centroid entries than the buffers hold: write nothing, report
+        if (j == 0 && threadIdx.x == 0) atomicOr(error, 1ull);
+        return;
+    }
     if (flag[j]) {
         const int64_t r = rrank[j];
         const int64_t ub = supoff[r], n = supend[r] - supoff[r];
@@ -317,6 +393,20 @@ __global__ void __launch_bounds__(WR_THREADS) k_write_rows(
 
 // Per-instance objective sums (one CTA per instance), fixed order:
 // per-thread strided partial sums, then a tree.
+// copy the new rows back over the current ones (fixed buffers for graph replay)
+__global__ void k_copy_back(int32_t k, int64_t cap, const int64_t *coff_src, const int32_t *term_src,
+                            const float *val_src, const double *sn_src, int64_t *coff_dst, int32_t *term_dst,
+                            float *val_dst, double *sn_dst) {
+    const int64_t n = min(coff_src[k], cap);
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = g; e < n; e += st) {
+        term_dst[e] = term_src[e];
+        val_dst[e] = val_src[e];
+    }
+    for (int64_t j = g; j <= k; j += st) coff_dst[j] = coff_src[j];
+    for (int64_t j = g; j < k; j += st) sn_dst[j] = sn_src[j];
+}
+
 __global__ void __launch_bounds__(1024) k_sum_inst(const int32_t *inst_k, const double *a, const double *b,
                                                    double *out) {
     __shared__ double sa[1024], sb[1024];
@@ -345,8 +435,9 @@ __global__ void __launch_bounds__(1024) k_sum_inst(const int32_t *inst_k, const 
 
 // ---------------- u5: structured inverted file ----------------
 
-__global__ void k_if_keys(int64_t n, const int32_t *cterm, const int32_t *cclu, const uint8_t *lam, uint32_t *keys,
-                          uint32_t *vals, uint32_t *cnt2) {
+__global__ void k_if_keys(const int64_t *n_dev, int64_t cap, const int32_t *cterm, const int32_t *cclu,
+                          const uint8_t *lam, uint32_t *keys, uint32_t *vals, uint32_t *cnt2) {
+    const int64_t n = min(*n_dev, cap);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t key = ((uint32_t)cterm[e] << 1) | (uint32_t)(lam[cclu[e]] ? 1 : 0);
         keys[e] = key;
@@ -365,9 +456,10 @@ __global__ void k_if_lens(int32_t D, const uint32_t *cnt2, int64_t *len, int32_t
 
 // if_cid holds global cluster ids; the scan arrays (if_cid16, if_pack) hold
 // ids local to the cluster's instance.
-__global__ void k_if_fill(int64_t n, const uint32_t *order, const int32_t *cclu, const int32_t *clu_koff,
-                          const float *cval, int prec, int32_t *if_cid, uint16_t *if_cid16, uint32_t *if_pack,
-                          float *if_val, uint16_t *if_lp) {
+__global__ void k_if_fill(const int64_t *n_dev, int64_t cap, const uint32_t *order, const int32_t *cclu,
+                          const int32_t *clu_koff, const float *cval, int prec, int32_t *if_cid, uint16_t *if_cid16,
+                          uint32_t *if_pack, float *if_val, uint16_t *if_lp) {
+    const int64_t n = min(*n_dev, cap);
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t e = order[q];
         const float u = cval[e];
@@ -419,6 +511,7 @@ cudaError_t init_centroids(sivf_ctx *c, const int32_t *init_ids_dev) {
     SIVF_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (tot > c->cap_c) return cudaErrorMemoryAllocation;
     c->c_nnz = tot;
+    c->if_nnz = tot;
     k_seed_rows<<<blocks_for((int64_t)c->k * 32), TPB, 0, c->stream>>>(c->k, init_ids_dev, c->row_ptr, c->idx,
                                                                        c->val, c->coff[cur], c->cterm[cur],
                                                                        c->cval[cur], c->cclu);
@@ -470,58 +563,61 @@ cudaError_t reseed_dev(sivf_ctx *c, const int32_t *init_ids_dev) {
     return cudaSuccess;
 }
 
+// Structured inverted file of the current centroids (count in coff[k], on the
+// device) with the current lambda. No host synchronisation.
 cudaError_t build_inverted_file(sivf_ctx *c) {
-    const int64_t n = c->c_nnz;
+    const int64_t cap = c->cap_c;
     const int cur = c->cur;
+    const int64_t *n_dev = c->coff[cur] + c->k;
     Workspace &ws = c->ws;
     size_t mark = ws.used;
     uint32_t *cnt2 = ws.take<uint32_t>((size_t)2 * c->D);
     int64_t *len = ws.take<int64_t>((size_t)c->D + 1);
     int64_t *total = ws.take<int64_t>(1);
-    uint32_t *k0 = ws.take<uint32_t>((size_t)n + 1), *v0 = ws.take<uint32_t>((size_t)n + 1);
-    uint32_t *k1 = ws.take<uint32_t>((size_t)n + 1), *v1 = ws.take<uint32_t>((size_t)n + 1);
+    uint32_t *k0 = ws.take<uint32_t>((size_t)cap + 1), *v0 = ws.take<uint32_t>((size_t)cap + 1);
+    uint32_t *k1 = ws.take<uint32_t>((size_t)cap + 1), *v1 = ws.take<uint32_t>((size_t)cap + 1);
     if (!cnt2 || !len || !total || !k0 || !v0 || !k1 || !v1) return cudaErrorMemoryAllocation;
     SIVF_CUDA_TRY(cudaMemsetAsync(cnt2, 0, sizeof(uint32_t) * 2 * c->D, c->stream));
-    if (n > 0) {
-        k_if_keys<<<blocks_for(n), TPB, 0, c->stream>>>(n, c->cterm[cur], c->cclu, c->lam, k0, v0, cnt2);
-        note_launch();
-    }
+    k_if_keys<<<blocks_for(cap), TPB, 0, c->stream>>>(n_dev, cap, c->cterm[cur], c->cclu, c->lam, k0, v0, cnt2);
     k_if_lens<<<blocks_for(c->D), TPB, 0, c->stream>>>(c->D, cnt2, len, c->if_mf0);
-    note_launch();
+    note_launch(2);
     SIVF_CUDA_TRY(cudaGetLastError());
     SIVF_CUDA_TRY(scan_exclusive_i64(len, c->if_off, c->D, total, ws, c->stream));
     SIVF_CUDA_TRY(cudaMemcpyAsync(c->if_off + c->D, total, sizeof(int64_t), cudaMemcpyDeviceToDevice, c->stream));
     bool alt = false;
-    SIVF_CUDA_TRY(radix_sort_pairs(k0, v0, k1, v1, n, c->bits_t + 1, &alt, ws, c->stream));
-    if (n > 0) {
-        k_if_fill<<<blocks_for(n), TPB, 0, c->stream>>>(n, alt ? v1 : v0, c->cclu, c->clu_koff, c->cval[cur], (int)c->cfg.prec,
-                                                       c->if_cid, c->if_cid16, c->if_pack, c->if_val, c->if_lp);
-        note_launch();
-    }
+    SIVF_CUDA_TRY(radix_sort_pairs_dev(k0, v0, k1, v1, cap, n_dev, c->bits_t + 1, &alt, ws, c->stream));
+    k_if_fill<<<blocks_for(cap), TPB, 0, c->stream>>>(n_dev, cap, alt ? v1 : v0, c->cclu, c->clu_koff, c->cval[cur],
+                                                      (int)c->cfg.prec, c->if_cid, c->if_cid16, c->if_pack, c->if_val,
+                                                      c->if_lp);
+    note_launch();
     SIVF_CUDA_TRY(cudaGetLastError());
-    c->if_nnz = n;
     ws.used = mark;
     return cudaSuccess;
 }
 
+// One update step (Algorithm 5). Every size that depends on the data stays on
+// the device, so the whole step can be captured in a CUDA graph.
 cudaError_t run_update(sivf_ctx *c) {
     cudaStream_t s = c->stream;
     Workspace &ws = c->ws;
     ws.reset();
     const int64_t N = c->N;
     const int32_t k = c->k;
-    const int old = c->cur, nw = 1 - c->cur;
+    const int64_t Tmax = c->nnz > 0 ? c->nnz : 1;
+    const int cur = c->cur, nw = 1 - c->cur;
 
     // u1: members grouped by cluster, ascending object id
     uint32_t *lk0 = ws.take<uint32_t>(N), *lv0 = ws.take<uint32_t>(N);
     uint32_t *lk1 = ws.take<uint32_t>(N), *lv1 = ws.take<uint32_t>(N);
     int64_t *cnt = ws.take<int64_t>(k), *flag = ws.take<int64_t>(k), *rrank = ws.take<int64_t>(k);
-    int64_t *nrec_d = ws.take<int64_t>(1), *tot_d = ws.take<int64_t>(1);
+    int64_t *nrec_d = ws.take<int64_t>(1), *T_d = ws.take<int64_t>(1), *newn_d = ws.take<int64_t>(1);
+    uint32_t *U_d = ws.take<uint32_t>(1);
     int64_t *sz = ws.take<int64_t>((size_t)k + 1);
     double *jAd = ws.take<double>(k), *jUd = ws.take<double>(k);
     int64_t *tc = ws.take<int64_t>(N), *toff = ws.take<int64_t>(N);
-    if (!lk0 || !lv0 || !lk1 || !lv1 || !cnt || !flag || !rrank || !nrec_d || !tot_d || !sz || !jAd || !jUd || !tc ||
-        !toff)
+    int64_t *ubeg = ws.take<int64_t>((size_t)k + 1), *uend = ws.take<int64_t>((size_t)k + 1);
+    if (!lk0 || !lv0 || !lk1 || !lv1 || !cnt || !flag || !rrank || !nrec_d || !T_d || !newn_d || !U_d || !sz ||
+        !jAd || !jUd || !tc || !toff || !ubeg || !uend)
         return cudaErrorMemoryAllocation;
     SIVF_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * k, s));
     k_label_keys<<<blocks_for(N), TPB, 0, s>>>(N, c->labels, lk0, lv0, cnt);
@@ -532,87 +628,83 @@ cudaError_t run_update(sivf_ctx *c) {
     k_recompute_flags<<<blocks_for(k), TPB, 0, s>>>(k, c->lam, cnt, flag);
     note_launch();
     SIVF_CUDA_TRY(scan_exclusive_i64(flag, rrank, k, nrec_d, ws, s));
-    int64_t nrec = 0;
-    SIVF_CUDA_TRY(cudaMemcpyAsync(&nrec, nrec_d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SIVF_CUDA_TRY(cudaStreamSynchronize(s));
 
-    // u2: per (cluster, term) sums for the recomputed clusters, in rank batches
-    int64_t *supoff = ws.take<int64_t>((size_t)nrec + 1), *supend = ws.take<int64_t>((size_t)nrec + 1);
-    const int64_t ucap = c->nnz + 1;
-    int32_t *uterm = ws.take<int32_t>((size_t)ucap);
-    double *usum = ws.take<double>((size_t)ucap);
-    if (!supoff || !supend || !uterm || !usum) return cudaErrorMemoryAllocation;
-    // a cluster whose members are all empty rows has no entries: begin = end = 0
-    SIVF_CUDA_TRY(cudaMemsetAsync(supoff, 0, sizeof(int64_t) * (nrec + 1), s));
-    SIVF_CUDA_TRY(cudaMemsetAsync(supend, 0, sizeof(int64_t) * (nrec + 1), s));
-    const int rbits_max = 32 - c->bits_t;
-    const int64_t batch = rbits_max >= 31 ? (int64_t)1 << 31 : (int64_t)1 << rbits_max;
-    int64_t ubase = 0, moved_nnz = 0;
-    for (int64_t r0 = 0; r0 < nrec; r0 += batch) {
-        const int64_t r1 = r0 + batch < nrec ? r0 + batch : nrec;
-        k_member_tuples<<<blocks_for(N), TPB, 0, s>>>(N, perm, c->labels, flag, rrank, r0, r1, c->row_ptr, tc);
-        note_launch();
-        SIVF_CUDA_TRY(scan_exclusive_i64(tc, toff, N, tot_d, ws, s));
-        int64_t T = 0;
-        SIVF_CUDA_TRY(cudaMemcpyAsync(&T, tot_d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        SIVF_CUDA_TRY(cudaStreamSynchronize(s));
-        moved_nnz += T;
-        if (T == 0) continue;
-        size_t mark = ws.used;
-        uint32_t *tk0 = ws.take<uint32_t>(T), *tv0 = ws.take<uint32_t>(T);
-        uint32_t *tk1 = ws.take<uint32_t>(T), *tv1 = ws.take<uint32_t>(T);
-        uint32_t *head = ws.take<uint32_t>(T), *uidx = ws.take<uint32_t>(T), *hpos = ws.take<uint32_t>(T);
-        double *part = ws.take<double>(T);
-        if (!tk0 || !tv0 || !tk1 || !tv1 || !head || !uidx || !hpos || !part) return cudaErrorMemoryAllocation;
-        k_expand<<<blocks_for(N * 32), TPB, 0, s>>>(N, perm, c->labels, rrank, r0, tc, toff, c->row_ptr, c->idx,
-                                                     c->val, c->bits_t, tk0, tv0);
-        note_launch();
-        const int nbits = bits_for((uint64_t)(r1 - r0 - 1)) + c->bits_t;
-        bool a2 = false;
-        SIVF_CUDA_TRY(radix_sort_pairs(tk0, tv0, tk1, tv1, T, nbits, &a2, ws, s));
-        const uint32_t *sk = a2 ? tk1 : tk0, *sv = a2 ? tv1 : tv0;
-        k_heads<<<blocks_for(T), TPB, 0, s>>>(T, sk, head);
-        note_launch();
-        SIVF_CUDA_TRY(scan_exclusive_u32(head, uidx, T, ws, s));
-        // U = uidx[T-1] + head[T-1]
-        uint32_t tail[2] = {0, 0};
-        SIVF_CUDA_TRY(cudaMemcpyAsync(&tail[0], uidx + (T - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        SIVF_CUDA_TRY(cudaMemcpyAsync(&tail[1], head + (T - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        k_head_pos<<<blocks_for(T), TPB, 0, s>>>(T, head, uidx, hpos);
-        note_launch();
-        SIVF_CUDA_TRY(cudaStreamSynchronize(s));
-        const int64_t U = (int64_t)tail[0] + (int64_t)tail[1];
-        k_seg_pieces<<<blocks_for((T + 31) / 32 * 32), TPB, 0, s>>>(T, sk, sv, part);
-        k_seg_runs<<<blocks_for(U), TPB, 0, s>>>(T, U, sk, hpos, part, ubase, c->bits_t, r0, uterm, usum, supoff,
-                                                  supend);
+    // u2: tuples of the recomputed clusters' members, in member order; a
+    // stable sort by term then a stable sort by cluster rank leave them in
+    // (rank, term, object) order; equal (rank, term) runs are summed in FP64
+    k_member_tuples<<<blocks_for(N), TPB, 0, s>>>(N, perm, c->labels, flag, c->row_ptr, tc);
+    note_launch();
+    SIVF_CUDA_TRY(scan_exclusive_i64(tc, toff, N, T_d, ws, s));
+    uint32_t *sa_k = ws.take<uint32_t>(Tmax), *sa_v = ws.take<uint32_t>(Tmax);
+    uint32_t *sb_k = ws.take<uint32_t>(Tmax), *sb_v = ws.take<uint32_t>(Tmax);
+    uint32_t *tterm = ws.take<uint32_t>(Tmax), *trank = ws.take<uint32_t>(Tmax);
+    float *tval = ws.take<float>(Tmax), *sval = ws.take<float>(Tmax);
+    unsigned long long *key64 = ws.take<unsigned long long>(Tmax);
+    double *part = ws.take<double>(Tmax);
+    int32_t *uterm = ws.take<int32_t>(Tmax);
+    double *usum = ws.take<double>(Tmax);
+    if (!sa_k || !sa_v || !sb_k || !sb_v || !tterm || !trank || !tval || !sval || !key64 || !part || !uterm || !usum)
+        return cudaErrorMemoryAllocation;
+    const int bits_r = bits_for((uint64_t)(k - 1));
+    if (bits_r + c->bits_tl <= 32) {
+        // one sort on (rank, local term) carrying the value bits
+        int32_t *rank2clu = reinterpret_cast<int32_t *>(tterm);
+        k_rank2clu<<<blocks_for(k), TPB, 0, s>>>(k, flag, rrank, rank2clu);
+        k_expand_packed<<<blocks_for(N * 32), TPB, 0, s>>>(N, perm, c->labels, rrank, tc, toff, c->row_ptr, c->idx,
+                                                            c->val, c->clu_doff, c->bits_tl, sa_k, sa_v);
         note_launch(2);
-        SIVF_CUDA_TRY(cudaGetLastError());
-        ubase += U;
-        ws.used = mark;
+        bool a1 = false;
+        SIVF_CUDA_TRY(radix_sort_pairs_dev(sa_k, sa_v, sb_k, sb_v, Tmax, T_d, bits_r + c->bits_tl, &a1, ws, s));
+        k_unpack<<<blocks_for(Tmax), TPB, 0, s>>>(Tmax, T_d, a1 ? sb_k : sa_k, a1 ? sb_v : sa_v, c->bits_tl, rank2clu,
+                                                  c->clu_doff, key64, sval);
+        note_launch();
+    } else {
+        // two stable sorts: by global term, then by rank
+        k_expand<<<blocks_for(N * 32), TPB, 0, s>>>(N, perm, c->labels, rrank, tc, toff, c->row_ptr, c->idx, c->val,
+                                                     sa_k, sa_v, tterm, tval, trank);
+        note_launch();
+        bool a1 = false;
+        SIVF_CUDA_TRY(radix_sort_pairs_dev(sa_k, sa_v, sb_k, sb_v, Tmax, T_d, c->bits_t, &a1, ws, s));
+        uint32_t *x_v = a1 ? sb_v : sa_v;                           // tuple ids sorted by term
+        uint32_t *y_k = a1 ? sa_k : sb_k, *y_v = a1 ? sa_v : sb_v;  // the free pair
+        uint32_t *z_k = a1 ? sb_k : sa_k;                           // its ping-pong partner
+        k_rank_keys<<<blocks_for(Tmax), TPB, 0, s>>>(Tmax, T_d, x_v, trank, y_k, y_v);
+        note_launch();
+        bool a2 = false;
+        SIVF_CUDA_TRY(radix_sort_pairs_dev(y_k, y_v, z_k, x_v, Tmax, T_d, bits_r, &a2, ws, s));
+        const uint32_t *r_k = a2 ? z_k : y_k, *r_v = a2 ? x_v : y_v;
+        k_compose<<<blocks_for(Tmax), TPB, 0, s>>>(Tmax, T_d, r_k, r_v, tterm, tval, key64, sval);
+        note_launch();
     }
-
-    // u3/u4: new cluster-major rows
-    k_new_sizes<<<blocks_for(k), TPB, 0, s>>>(k, flag, rrank, supoff, supend, c->coff[old], sz);
+    // the sort buffers are free again: run flags, run index, run position
+    uint32_t *head = sa_k, *uidx = sa_v, *hpos = sb_k;
+    k_heads<<<blocks_for(Tmax), TPB, 0, s>>>(Tmax, T_d, key64, head);
     note_launch();
-    SIVF_CUDA_TRY(scan_exclusive_i64(sz, c->coff[nw], k, tot_d, ws, s));
-    SIVF_CUDA_TRY(cudaMemcpyAsync(c->coff[nw] + k, tot_d, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-    int64_t newn = 0;
-    SIVF_CUDA_TRY(cudaMemcpyAsync(&newn, tot_d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SIVF_CUDA_TRY(cudaStreamSynchronize(s));
-    if (newn > c->cap_c || newn >= 0x7FFFFFFFll - 2 * IF_PAD) return cudaErrorMemoryAllocation;
-    k_write_rows<<<(unsigned)k, WR_THREADS, 0, s>>>(
-        k, flag, rrank, supoff, supend, uterm, usum, cnt, c->coff[old], c->cterm[old], c->cval[old], c->snorm,
-        c->coff[nw], c->cterm[nw], c->cval[nw], c->cclu, c->snorm_new, jAd, jUd);
-    note_launch();
-    k_sum_inst<<<(unsigned)c->n_inst, 1024, 0, s>>>(c->inst_k, jAd, jUd, c->obj_dev);
-    note_launch();
+    SIVF_CUDA_TRY(scan_exclusive_u32_dev(head, uidx, Tmax, T_d, U_d, ws, s));
+    SIVF_CUDA_TRY(cudaMemsetAsync(ubeg, 0, sizeof(int64_t) * (k + 1), s));  // empty-row clusters: no entries
+    SIVF_CUDA_TRY(cudaMemsetAsync(uend, 0, sizeof(int64_t) * (k + 1), s));
+    k_head_pos<<<blocks_for(Tmax), TPB, 0, s>>>(Tmax, T_d, head, uidx, hpos);
+    k_seg_pieces<<<blocks_for((Tmax + 31) / 32 * 32), TPB, 0, s>>>(Tmax, T_d, key64, sval, part);
+    k_seg_runs<<<blocks_for(Tmax), TPB, 0, s>>>(Tmax, T_d, U_d, key64, hpos, part, uterm, usum, ubeg, uend);
+    note_launch(3);
     SIVF_CUDA_TRY(cudaGetLastError());
-    c->cur = nw;
-    c->c_nnz = newn;
-    double *t = c->snorm;
-    c->snorm = c->snorm_new;
-    c->snorm_new = t;
-    c->stats.moved_nnz = moved_nnz;
+
+    // u3/u4: new cluster-major rows (into the second buffer), copied back
+    k_new_sizes<<<blocks_for(k), TPB, 0, s>>>(k, flag, rrank, ubeg, uend, c->coff[cur], sz);
+    note_launch();
+    SIVF_CUDA_TRY(scan_exclusive_i64(sz, c->coff[nw], k, newn_d, ws, s));
+    SIVF_CUDA_TRY(cudaMemcpyAsync(c->coff[nw] + k, newn_d, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    k_write_rows<<<(unsigned)k, WR_THREADS, 0, s>>>(
+        k, flag, rrank, ubeg, uend, uterm, usum, cnt, c->coff[cur], c->cterm[cur], c->cval[cur], c->snorm,
+        c->coff[nw], c->cterm[nw], c->cval[nw], c->cclu, c->snorm_new, jAd, jUd, c->cap_c, &c->ctr->error);
+    k_sum_inst<<<(unsigned)c->n_inst, 1024, 0, s>>>(c->inst_k, jAd, jUd, c->obj_dev);
+    k_copy_back<<<blocks_for(c->cap_c), TPB, 0, s>>>(k, c->cap_c, c->coff[nw], c->cterm[nw], c->cval[nw],
+                                                     c->snorm_new, c->coff[cur], c->cterm[cur], c->cval[cur],
+                                                     c->snorm);
+    note_launch(3);
+    SIVF_CUDA_TRY(cudaGetLastError());
+    SIVF_CUDA_TRY(cudaMemcpyAsync(&c->ctr->moved, T_d, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    SIVF_CUDA_TRY(cudaMemcpyAsync(&c->ctr->c_nnz, newn_d, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     ws.reset();
 
     // u5: rebuild the structured inverted file with lambda^[r]
@@ -620,5 +712,4 @@ cudaError_t run_update(sivf_ctx *c) {
     ws.reset();
     return cudaSuccess;
 }
-
 }  // namespace sivf

@@ -20,7 +20,7 @@ PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
 
 class sivf_config(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("icp", ctypes.c_int), ("threads", ctypes.c_int),
-                ("ctas_per_sm", ctypes.c_int), ("mem_cap_bytes", ctypes.c_int64)]
+                ("ctas_per_sm", ctypes.c_int), ("mem_cap_bytes", ctypes.c_int64), ("use_graph", ctypes.c_int)]
 
 
 class sivf_stats(ctypes.Structure):
@@ -29,7 +29,8 @@ class sivf_stats(ctypes.Structure):
                 ("postings", ctypes.c_int64), ("rescored", ctypes.c_int64), ("rescore_cands", ctypes.c_int64),
                 ("centroid_nnz", ctypes.c_int64), ("moved_nnz", ctypes.c_int64),
                 ("objective_assign", ctypes.c_double), ("objective_update", ctypes.c_double),
-                ("ms_assign", ctypes.c_double), ("ms_update", ctypes.c_double), ("launches", ctypes.c_int64)]
+                ("ms_assign", ctypes.c_double), ("ms_update", ctypes.c_double), ("launches", ctypes.c_int64),
+                ("graph_iters", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -193,7 +194,7 @@ class SIVF:
     """
 
     def __init__(self, row_ptr, idx, val, D: int, k: int, init_ids, precision: str = "fp32", icp: bool = True,
-                 threads: int = 0, ctas_per_sm: int = 0, mem_cap_bytes: int = 0, stream=None):
+                 threads: int = 0, ctas_per_sm: int = 0, mem_cap_bytes: int = 0, stream=None, use_graph: bool = False):
         import numpy as np
         import torch
 
@@ -211,7 +212,8 @@ class SIVF:
         self.D, self.k = int(D), int(k)
         ini = np.ascontiguousarray(np.asarray(init_ids, dtype=np.int32))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        cfg = sivf_config(PRECISIONS[precision], int(bool(icp)), int(threads), int(ctas_per_sm), int(mem_cap_bytes))
+        cfg = sivf_config(PRECISIONS[precision], int(bool(icp)), int(threads), int(ctas_per_sm), int(mem_cap_bytes),
+                          int(bool(use_graph)))
         self.ctx = sivf_init(cfg, self.N, self.D, self.k, self.row_ptr.data_ptr(), self.idx.data_ptr(),
                              self.val.data_ptr(), ini.ctypes.data, self.stream.cuda_stream)
 
@@ -242,6 +244,12 @@ class SIVF:
 
     def stats(self) -> dict:
         return sivf_get_stats(self.ctx).as_dict()
+
+    def last_error(self) -> str:
+        return (load().sivf_last_error(self.ctx) or b"").decode(errors="replace")
+
+    def last_error(self) -> str:
+        return (load().sivf_last_error(self.ctx) or b"").decode(errors="replace")
 
     def labels(self):
         import numpy as np
@@ -327,7 +335,7 @@ class SIVFBatch:
     """
 
     def __init__(self, corpora, ks, init_ids, precision: str = "fp32", icp: bool = True, threads: int = 0,
-                 ctas_per_sm: int = 0):
+                 ctas_per_sm: int = 0, use_graph: bool = False):
         import numpy as np
         import torch
 
@@ -345,7 +353,8 @@ class SIVFBatch:
         self.n_inst = len(descs)
         self.Ns = [d.N for d in descs]
         self.ks = [int(k) for k in ks]
-        cfg = sivf_config(PRECISIONS[precision], int(bool(icp)), int(threads), int(ctas_per_sm), 0)
+        cfg = sivf_config(PRECISIONS[precision], int(bool(icp)), int(threads), int(ctas_per_sm), 0,
+                          int(bool(use_graph)))
         self.ctx = sivf_batch_init(cfg, descs)
         self._keep = None  # the library copied the corpora
 
@@ -391,3 +400,6 @@ class SIVFBatch:
 
     def stats(self) -> dict:
         return sivf_get_stats(self.ctx).as_dict()
+
+    def last_error(self) -> str:
+        return (load().sivf_last_error(self.ctx) or b"").decode(errors="replace")

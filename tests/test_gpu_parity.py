@@ -210,3 +210,51 @@ def test_batched_run_equals_separate_runs():
                 g.close()
     finally:
         b.close()
+
+
+def test_graph_loop_equals_host_stepped_run():
+    """With use_graph the iterations after the second run inside one CUDA graph
+    (WHILE conditional node): same labels, iteration count, objective and
+    centroids as the host-stepped run."""
+    w = CONFIGS["c2"].scaled(N=8_000, D=10_000, k=80)
+    c, ini = corpus_for(w, seed=17)
+    a = gpu_instance(c, w.k, ini, use_graph=False)
+    b = gpu_instance(c, w.k, ini, use_graph=True)
+    try:
+        ia, oa = a.run(40)
+        ib, ob = b.run(40)
+        assert b.stats()["graph_iters"] > 0, b.last_error()
+        assert a.stats()["graph_iters"] == 0
+        assert ia == ib
+        assert np.array_equal(a.labels(), b.labels())
+        assert oa == ob
+        for x, y in zip(a.centroids(), b.centroids()):
+            assert np.array_equal(x, y)
+        # a second call continues from the converged state identically
+        assert a.run(5)[0] == b.run(5)[0]
+        # reseeding reuses the captured graph
+        a.reseed(ini)
+        b.reseed(ini)
+        assert a.run(40) == b.run(40)
+        assert np.array_equal(a.labels(), b.labels())
+    finally:
+        a.close()
+        b.close()
+
+
+def test_graph_loop_batched_equals_host_stepped():
+    from paper_2103_16141_gb300 import SIVFBatch
+    ws, cs, inis = _batch_corpora(5, scale=0.04, seed0=200)
+    a = SIVFBatch(cs, [w.k for w in ws], inis, precision="fp16", use_graph=False)
+    b = SIVFBatch(cs, [w.k for w in ws], inis, precision="fp16", use_graph=True)
+    try:
+        ia, oa = a.run(50)
+        ib, ob = b.run(50)
+        assert b.stats()["graph_iters"] > 0, b.last_error()
+        assert np.array_equal(ia, ib)
+        assert np.array_equal(oa, ob)
+        for m in range(len(ws)):
+            assert np.array_equal(a.labels(m), b.labels(m))
+    finally:
+        a.close()
+        b.close()
