@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--graph", type=int, default=1, help="1: iterations after the second run in one CUDA graph")
+    ap.add_argument("--autotune", type=int, default=1, help="1: pick the assignment kernel configuration by timing")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-iters", type=int, default=8)
@@ -252,7 +253,7 @@ def run_batched(args):
     cs = [generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, w.seed) for w in ws]
     inis = [init_ids(w.N, w.k, w.init_seed) for w in ws]
     b = SIVFBatch(cs, [w.k for w in ws], inis, precision=prec, icp=bool(args.icp), threads=args.threads,
-                  ctas_per_sm=args.ctas_per_sm, use_graph=bool(args.graph))
+                  ctas_per_sm=args.ctas_per_sm, use_graph=bool(args.graph), autotune=bool(args.autotune))
     gini = np.ascontiguousarray(np.concatenate([ini + off for ini, off in
                                                 zip(inis, np.cumsum([0] + [w.N for w in ws[:-1]]))]), dtype=np.int32)
     max_iter = ws[0].max_iter
@@ -322,7 +323,8 @@ def main():
     ini = init_ids(w.N, w.k, w.init_seed)
     dev = torch.device("cuda", torch.cuda.current_device())
     g = SIVF(c.row_ptr, c.idx, c.val, c.D, w.k, ini, precision=w.precision, icp=bool(args.icp),
-             threads=args.threads, ctas_per_sm=args.ctas_per_sm, use_graph=bool(args.graph))
+             threads=args.threads, ctas_per_sm=args.ctas_per_sm, use_graph=bool(args.graph),
+             autotune=bool(args.autotune))
     stream = torch.cuda.current_stream()
 
     def one_run_stepped():
@@ -407,7 +409,8 @@ def main():
             d_ix = ix.to(dev, non_blocking=True)
             d_vl = vl.to(dev, non_blocking=True)
             ge = SIVF(d_rp, d_ix, d_vl, c.D, w.k, ini, precision=w.precision, icp=bool(args.icp),
-                      threads=args.threads, ctas_per_sm=args.ctas_per_sm, use_graph=bool(args.graph))
+                      threads=args.threads, ctas_per_sm=args.ctas_per_sm, use_graph=bool(args.graph),
+             autotune=bool(args.autotune))
             it, _ = ge.run(w.max_iter)
             e_iters += it
             S.sivf_get_labels(ge.ctx, lab_host.data_ptr(), False)
@@ -434,7 +437,9 @@ def main():
                        "iters_per_step": iters_per_step, "sec_per_iter": ms / 1e3 / tot_iters,
                        "l2": "inputs larger than L2 (CSR 0.46 GB; inverted file > 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "cuda_graph": bool(args.graph)},
+                       "cuda_graph": bool(args.graph), "autotune": bool(args.autotune),
+                       "assign_threads": g.stats()["assign_threads"],
+                       "score_buffer": "global" if g.stats()["assign_global"] else "shared"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": traffic, "traffic_launch": traffic_launch,
                          "peak_source": peak_src, "kernel": "assign_kernel",

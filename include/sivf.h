@@ -61,6 +61,11 @@ typedef struct {
                             replay one CUDA graph whose conditional WHILE node runs the
                             remaining iterations on the device (no per-iteration host
                             round trip); 0: every step launched from the host */
+    int autotune;        /* 1: at the second assignment, time every feasible assignment
+                            kernel configuration (threads per CTA x score vector in shared
+                            or global memory) on the live state and keep the fastest;
+                            threads / ctas_per_sm then only seed the search */
+    int score_buffer;    /* 0: automatic (shared memory when k fits), 1: shared, 2: global */
 } sivf_config;
 
 /* Counters of the most recent assignment / update (host copy). */
@@ -82,6 +87,8 @@ typedef struct {
     double ms_update;        /* device time of the last update step */
     int64_t launches;        /* kernels launched by the library since sivf_init / sivf_reseed */
     int64_t graph_iters;     /* iterations the last sivf_run / sivf_batch_run ran inside its CUDA graph */
+    int32_t assign_threads;  /* threads per CTA of the assignment kernel in use */
+    int32_t assign_global;   /* 1 if its score vectors live in global memory */
 } sivf_stats;
 
 typedef struct sivf_ctx sivf_ctx; /* opaque, library-owned */

@@ -52,7 +52,7 @@ void free_all(sivf_ctx *c) {
                     c->cval[0], c->cval[1], c->cclu, c->if_off, c->if_mf0, c->if_cid, c->if_cid16, c->if_pack, c->if_val, c->if_lp,
                     c->ctr, c->obj_dev, c->ws.base, c->inst_obj, c->inst_k, c->mov_beg, c->clu_koff,
                     c->inst_changed, c->own_row_ptr, c->own_idx, c->own_val, c->clu_doff,
-                    c->loop_dev, c->done_dev, c->objf_dev};
+                    c->loop_dev, c->done_dev, c->objf_dev, c->grho};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     destroy_loop_graph(c);
@@ -72,9 +72,14 @@ sivf_status check_usable(sivf_ctx *c) {
 void pick_assign_config(sivf_ctx *c) {
     int T = c->cfg.threads;
     if (T != 64 && T != 128 && T != 256 && T != 512) T = 0;
-    if (T == 0) T = c->k <= 256 ? 64 : (c->k <= 4096 ? 128 : 512);
+    if (T == 0) T = c->kmax <= 256 ? 64 : (c->kmax <= 4096 ? 128 : 512);
     c->assign_threads = T;
     c->assign_ctas_per_sm = c->cfg.ctas_per_sm > 0 ? c->cfg.ctas_per_sm : 0;
+    int dev = 0, smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const bool fits = ((size_t)((c->kmax + 3) & ~3) * 4 + (size_t)T * 16) <= (size_t)smem;
+    c->assign_global = c->cfg.score_buffer == 2 || (c->cfg.score_buffer == 0 && !fits) ? 1 : 0;
 }
 
 }  // namespace
@@ -130,8 +135,6 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
         delete c;
         return SIVF_ERR_INVALID_ARG;
     }
-    pick_assign_config(c);
-
     cudaError_t e;
 #define INIT_CUDA(expr, where)                      \
     do {                                            \
@@ -145,6 +148,7 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
     } while (0)
     INIT_CUDA(cudaGetDevice(&c->device), "cudaGetDevice");
     INIT_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device), "attr");
+    pick_assign_config(c);
     // nnz from row_ptr[N]
     int64_t nnz = 0, first = 0;
     INIT_CUDA(cudaMemcpyAsync(&nnz, row_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream), "read nnz");
@@ -200,6 +204,13 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
     INIT_CUDA(cudaMallocHost(reinterpret_cast<void **>(&c->nmov_pin), sizeof(int32_t)), "alloc host");
     INIT_CUDA(cudaMallocHost(reinterpret_cast<void **>(&c->loop_pin), sizeof(int32_t) * (4 + (size_t)ni)), "alloc host");
     INIT_CUDA(cudaMallocHost(reinterpret_cast<void **>(&c->objf_pin), sizeof(double) * ni), "alloc host");
+    if (c->assign_global || c->cfg.autotune) {
+        // global score vectors: one kmax slab per resident CTA (at most 16 per SM)
+        c->grho_ctas = (int64_t)c->num_sms * 16;
+        INIT_CUDA(dmalloc(c, &c->grho, (size_t)c->grho_ctas * ((c->kmax + 3) & ~3)), "alloc");
+        INIT_CUDA(cudaMemsetAsync(c->grho, 0, sizeof(uint32_t) * (size_t)c->grho_ctas * ((c->kmax + 3) & ~3),
+                                  c->stream), "memset");
+    }
     INIT_CUDA(dmalloc(c, &c->loop_dev, 4), "alloc");
     INIT_CUDA(dmalloc(c, &c->done_dev, ni), "alloc");
     INIT_CUDA(dmalloc(c, &c->objf_dev, ni), "alloc");
@@ -576,6 +587,7 @@ sivf_status sivf_assign(sivf_ctx *c, int64_t *n_changed) {
         return fail(c, SIVF_ERR_STATE,
                     "sivf_update must run between two assignments (and after sivf_set_labels)");
     c->iter += 1;
+    if (c->cfg.autotune && !c->tuned && c->iter == 2) API_CUDA(c, autotune_assign(c), "autotune");
     API_CUDA(c, enqueue_assign(c, true), "assignment");
     API_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
     float ms = 0.f;
@@ -734,6 +746,8 @@ sivf_status sivf_get_lambda(sivf_ctx *c, uint8_t *dst) {
 sivf_status sivf_get_stats(sivf_ctx *c, sivf_stats *out) {
     if (!c || !out) return SIVF_ERR_INVALID_ARG;
     c->stats.launches = (int64_t)(g_launches - c->launch_base);
+    c->stats.assign_threads = c->assign_threads;
+    c->stats.assign_global = c->assign_global;
     *out = c->stats;
     return SIVF_OK;
 }

@@ -50,6 +50,7 @@ struct AssignParams {
     const int32_t *if_cid;
     const uint16_t *if_cid16;
     const uint32_t *if_pack;   // (id << 16) | bf16/fp16 bits, when k <= 65536 and values are 16-bit
+    uint32_t *grho;            // global score vectors, one kmax slab per CTA (global score-buffer variant)
     const void *if_vals;
     const int64_t *coff;
     const int32_t *cterm;
@@ -208,15 +209,32 @@ __device__ __forceinline__ float decode_u(unsigned short b) {
 #define SIVF_ASSIGN_MIN_CTAS_128 10
 #endif
 
-template <int T, int PREC, bool CID16>
+// Score-vector reads and resets. A global score vector is updated by L2
+// atomics, so its plain reads and stores must not go through L1 (which is not
+// coherent with them): they use the L2-only (.cg) forms.
+template <bool GRHO>
+__device__ __forceinline__ uint32_t rho_ld(const uint32_t *p) {
+    if constexpr (GRHO) return __ldcg(p);
+    else return *p;
+}
+template <bool GRHO>
+__device__ __forceinline__ void rho_zero(uint32_t *p) {
+    if constexpr (GRHO) __stcg(p, 0u);
+    else *p = 0u;
+}
+
+// GRHO: the score vector lives in global memory (a kmax slab per CTA, L2
+// atomics) instead of shared memory; slower per posting, but independent of
+// the shared-memory size, so it serves any k and lets more CTAs reside.
+template <int T, int PREC, bool CID16, bool GRHO>
 __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) : 1)
     assign_kernel(AssignParams P) {
     constexpr bool PACKED = CID16 && PREC != SIVF_FP32;
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int NW = T / 32;
     const int kpad = (P.kmax + 3) & ~3;
-    uint32_t *rho = smem;
-    float *s_vs = reinterpret_cast<float *>(smem + kpad);
+    uint32_t *rho = GRHO ? P.grho + (size_t)blockIdx.x * kpad : smem;
+    float *s_vs = reinterpret_cast<float *>(GRHO ? smem : smem + kpad);
     int *s_start = reinterpret_cast<int *>(s_vs + T);
     int *s_len = s_start + T;
     int *s_item = s_len + T;
@@ -231,7 +249,7 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
     __shared__ uint32_t s_thr;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int j = tid; j < kpad; j += T) rho[j] = 0u;
+    for (int j = tid; j < kpad; j += T) rho_zero<GRHO>(rho + j);
     unsigned long long c_post_obj = 0, c_filt = 0, c_sim = 0, c_resc = 0, c_cand = 0, c_chg = 0;
     __syncthreads();
 
@@ -363,11 +381,11 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
         t.sv = -1;
         // candidates by local id (same order as global ids within the instance)
         if (!filt) {
-            for (int j = tid; j < km; j += T) top2_push(t, rho[j], j);
+            for (int j = tid; j < km; j += T) top2_push(t, rho_ld<GRHO>(rho + j), j);
         } else {
             for (int m = tid; m < n_mov; m += T) {
                 const int j = movs[m] - k_off;
-                top2_push(t, rho[j], j);
+                top2_push(t, rho_ld<GRHO>(rho + j), j);
             }
             if (tid == 0) top2_push(t, own_q, a_loc);
         }
@@ -408,7 +426,7 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
                 int j = -1;
                 if (m < total) {
                     j = filt ? movs[m] - k_off : m;
-                    if (rho[j] < thr) j = -1;
+                    if (rho_ld<GRHO>(rho + j) < thr) j = -1;
                 }
                 unsigned bal = __ballot_sync(0xffffffffu, j >= 0);
                 while (bal) {
@@ -457,7 +475,7 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
             const int al = s_winner;  // local id
             const int a = k_off + al;
             P.labels[i] = a;
-            P.own[i] = (filt && al == a_loc) ? own_q : rho[al];
+            P.own[i] = (filt && al == a_loc) ? own_q : rho_ld<GRHO>(rho + al);
             if (a != a_prev) {
                 c_chg += 1;
                 P.moving[a] = 1;
@@ -469,9 +487,9 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
         }
         __syncthreads();
         if (!filt) {
-            for (int j = tid; j < km; j += T) rho[j] = 0u;
+            for (int j = tid; j < km; j += T) rho_zero<GRHO>(rho + j);
         } else {
-            for (int m = tid; m < n_mov; m += T) rho[movs[m] - k_off] = 0u;
+            for (int m = tid; m < n_mov; m += T) rho_zero<GRHO>(rho + (movs[m] - k_off));
         }
         __syncthreads();
     }
@@ -528,11 +546,11 @@ __global__ void __launch_bounds__(1024) finalize_kernel(int32_t k, int first_ite
     }
 }
 
-template <int T, int PREC, bool CID16>
+template <int T, int PREC, bool CID16, bool GRHO>
 cudaError_t launch_t(sivf_ctx *c, const AssignParams &P, int ctas_per_sm) {
     const int kpad = (c->kmax + 3) & ~3;
-    const size_t smem = (size_t)kpad * 4 + (size_t)T * 16;
-    auto kern = assign_kernel<T, PREC, CID16>;
+    const size_t smem = (GRHO ? 0 : (size_t)kpad * 4) + (size_t)T * 16;
+    auto kern = assign_kernel<T, PREC, CID16, GRHO>;
     // the attribute and occupancy queries are host calls that a stream capture
     // refuses: they run on the first (host-launched) step and are cached
     if (c->assign_grid <= 0) {
@@ -541,27 +559,31 @@ cudaError_t launch_t(sivf_ctx *c, const AssignParams &P, int ctas_per_sm) {
         SIVF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, smem));
         if (occ < 1) return cudaErrorInvalidConfiguration;
         int per_sm = ctas_per_sm > 0 ? min(ctas_per_sm, occ) : occ;
-        c->assign_grid = min((int64_t)c->num_sms * per_sm, c->N);
+        int64_t grid = min((int64_t)c->num_sms * per_sm, c->N);
+        if (GRHO) grid = min(grid, c->grho_ctas);  // one slab per CTA
+        c->assign_grid = grid;
     }
     kern<<<(unsigned)c->assign_grid, T, smem, c->stream>>>(P);
     note_launch();
     return cudaGetLastError();
 }
 
-template <int PREC, bool CID16>
+template <int PREC, bool CID16, bool GRHO>
 cudaError_t launch_prec(sivf_ctx *c, const AssignParams &P) {
     const int cps = c->assign_ctas_per_sm;
     switch (c->assign_threads) {
-        case 64: return launch_t<64, PREC, CID16>(c, P, cps);
-        case 128: return launch_t<128, PREC, CID16>(c, P, cps);
-        case 256: return launch_t<256, PREC, CID16>(c, P, cps);
-        default: return launch_t<512, PREC, CID16>(c, P, cps);
+        case 64: return launch_t<64, PREC, CID16, GRHO>(c, P, cps);
+        case 128: return launch_t<128, PREC, CID16, GRHO>(c, P, cps);
+        case 256: return launch_t<256, PREC, CID16, GRHO>(c, P, cps);
+        default: return launch_t<512, PREC, CID16, GRHO>(c, P, cps);
     }
 }
 
 template <int PREC>
 cudaError_t launch_ids(sivf_ctx *c, const AssignParams &P) {
-    return P.if_cid16 ? launch_prec<PREC, true>(c, P) : launch_prec<PREC, false>(c, P);
+    if (c->assign_global)
+        return P.if_cid16 ? launch_prec<PREC, true, true>(c, P) : launch_prec<PREC, false, true>(c, P);
+    return P.if_cid16 ? launch_prec<PREC, true, false>(c, P) : launch_prec<PREC, false, false>(c, P);
 }
 
 }  // namespace
@@ -580,6 +602,7 @@ cudaError_t launch_assign(sivf_ctx *c) {
     P.if_cid = c->if_cid;
     P.if_cid16 = c->if_cid16;
     P.if_pack = c->if_pack;
+    P.grho = c->grho;
     P.if_vals = c->cfg.prec == SIVF_FP32 ? (const void *)c->if_val : (const void *)c->if_lp;
     P.coff = c->coff[c->cur];
     P.cterm = c->cterm[c->cur];
@@ -612,6 +635,82 @@ cudaError_t launch_assign(sivf_ctx *c) {
         case SIVF_FP16: return launch_ids<SIVF_FP16>(c, P);
         default: return launch_ids<SIVF_FP32>(c, P);
     }
+}
+
+// Autotuner of the assignment kernel: times every feasible (threads per CTA,
+// score buffer in shared or global memory) configuration on the live state
+// and keeps the fastest. The kernel writes labels, own scores, moving flags
+// and counters; those are restored (or reset) around each trial, so the step
+// that follows sees the state it would have seen without tuning.
+cudaError_t autotune_assign(sivf_ctx *c) {
+    cudaStream_t s = c->stream;
+    Workspace &ws = c->ws;
+    ws.reset();
+    uint32_t *own_snap = ws.take<uint32_t>((size_t)c->N);
+    int32_t *lab_snap = ws.take<int32_t>((size_t)c->N);
+    if (!own_snap || !lab_snap) return cudaErrorMemoryAllocation;
+    SIVF_CUDA_TRY(cudaMemcpyAsync(own_snap, c->own, sizeof(uint32_t) * c->N, cudaMemcpyDeviceToDevice, s));
+    SIVF_CUDA_TRY(cudaMemcpyAsync(lab_snap, c->labels, sizeof(int32_t) * c->N, cudaMemcpyDeviceToDevice, s));
+    // the trial steps read a^[r-1] and lambda^[r-1] as the real step will
+    SIVF_CUDA_TRY(cudaMemcpyAsync(c->labels_prev, c->labels, sizeof(int32_t) * c->N, cudaMemcpyDeviceToDevice, s));
+    SIVF_CUDA_TRY(cudaMemcpyAsync(c->lam_prev, c->lam, c->k, cudaMemcpyDeviceToDevice, s));
+    int dev_smem = 0;
+    SIVF_CUDA_TRY(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    const int kpad = (c->kmax + 3) & ~3;
+    const int threads[4] = {64, 128, 256, 512};
+    const int def_t = c->assign_threads, def_g = c->assign_global;
+    float best = 1e30f, def_ms = 1e30f;
+    int best_t = def_t, best_g = def_g;
+    cudaEvent_t e0 = c->ev[0], e1 = c->ev[1];
+    for (int g = 0; g < 2; ++g) {
+        if (g == 1 && !c->grho) continue;
+        for (int t : threads) {
+            if (!g && (size_t)kpad * 4 + (size_t)t * 16 > (size_t)dev_smem) continue;
+            float trial = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {  // best of two launches
+            SIVF_CUDA_TRY(cudaMemcpyAsync(c->own, own_snap, sizeof(uint32_t) * c->N, cudaMemcpyDeviceToDevice, s));
+            SIVF_CUDA_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
+            SIVF_CUDA_TRY(cudaMemsetAsync(c->moving, 0, c->k, s));
+            SIVF_CUDA_TRY(cudaMemsetAsync(c->inst_changed, 0, sizeof(unsigned long long) * c->n_inst, s));
+            if (g) SIVF_CUDA_TRY(cudaMemsetAsync(c->grho, 0, sizeof(uint32_t) * (size_t)c->grho_ctas * kpad, s));
+            c->assign_threads = t;
+            c->assign_global = g;
+            c->assign_grid = 0;
+            SIVF_CUDA_TRY(cudaEventRecord(e0, s));
+            cudaError_t e = launch_assign(c);
+            SIVF_CUDA_TRY(cudaEventRecord(e1, s));
+            SIVF_CUDA_TRY(cudaStreamSynchronize(s));
+            if (e != cudaSuccess) {  // configuration not launchable here: skip it
+                cudaGetLastError();
+                break;
+            }
+            float ms = 0.f;
+            SIVF_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            trial = ms < trial ? ms : trial;
+            }
+            if (t == def_t && g == def_g) def_ms = trial;
+            if (trial < best) {
+                best = trial;
+                best_t = t;
+                best_g = g;
+            }
+        }
+    }
+    // keep the default unless the winner is clearly faster (timing noise)
+    if (def_ms < 1e29f && best > 0.97f * def_ms) {
+        best_t = def_t;
+        best_g = def_g;
+    }
+    c->assign_threads = best_t;
+    c->assign_global = best_g;
+    c->assign_grid = 0;
+    c->tuned = true;
+    SIVF_CUDA_TRY(cudaMemcpyAsync(c->own, own_snap, sizeof(uint32_t) * c->N, cudaMemcpyDeviceToDevice, s));
+    SIVF_CUDA_TRY(cudaMemcpyAsync(c->labels, lab_snap, sizeof(int32_t) * c->N, cudaMemcpyDeviceToDevice, s));
+    if (best_g) SIVF_CUDA_TRY(cudaMemsetAsync(c->grho, 0, sizeof(uint32_t) * (size_t)c->grho_ctas * kpad, s));
+    SIVF_CUDA_TRY(cudaStreamSynchronize(s));
+    ws.reset();
+    return cudaSuccess;
 }
 
 cudaError_t launch_finalize_assign(sivf_ctx *c) {

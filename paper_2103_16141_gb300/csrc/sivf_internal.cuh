@@ -130,6 +130,10 @@ struct sivf_ctx {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int assign_threads = 0, assign_ctas_per_sm = 0;
     int64_t assign_grid = 0;  // cached launch grid of the assignment kernel (0 = not yet chosen)
+    int assign_global = 0;    // 1: score vectors in global memory (grho), else shared memory
+    bool tuned = false;       // the autotuner has picked the assignment configuration
+    uint32_t *grho = nullptr; // global score vectors: grho_ctas slabs of kmax (zero between objects)
+    int64_t grho_ctas = 0;
     unsigned long long launch_base = 0;  // g_launches at init / reseed
 
     // independent instances sharing one context: objects [inst_obj[m],
@@ -194,6 +198,7 @@ int bits_for(uint64_t max_value);  // number of bits to hold values in [0, max_v
 // ---- assign.cu ----
 cudaError_t launch_assign(sivf_ctx *c);
 cudaError_t launch_finalize_assign(sivf_ctx *c);
+cudaError_t autotune_assign(sivf_ctx *c);
 
 // ---- graph.cu ----
 cudaError_t build_loop_graph(sivf_ctx *c);

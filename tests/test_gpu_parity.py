@@ -258,3 +258,28 @@ def test_graph_loop_batched_equals_host_stepped():
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("score_buffer", ["global"])
+def test_global_score_buffer_matches_oracle(score_buffer):
+    w = CONFIGS["c2"].scaled(N=4_000, D=6_000, k=70)
+    c, ini = corpus_for(w, seed=23)
+    lockstep(c, w.k, ini, 6, score_buffer=score_buffer)
+
+
+def test_autotuned_run_equals_default_run():
+    """The autotuner's trial launches leave no trace: the tuned run produces
+    the default run's labels and iteration count."""
+    w = CONFIGS["c2"].scaled(N=8_000, D=10_000, k=80)
+    c, ini = corpus_for(w, seed=29)
+    a = gpu_instance(c, w.k, ini)
+    b = gpu_instance(c, w.k, ini, autotune=True)
+    try:
+        ra, rb = a.run(40), b.run(40)
+        assert ra == rb
+        assert np.array_equal(a.labels(), b.labels())
+        st = b.stats()
+        assert st["assign_threads"] in (64, 128, 256, 512)
+    finally:
+        a.close()
+        b.close()
