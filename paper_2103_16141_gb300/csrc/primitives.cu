@@ -134,13 +134,19 @@ constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 4096
 constexpr int RS_MAX_BITS = 10;                 // digit width of one pass (<= 1024 buckets)
 
+// Histograms are stored digit-major with the live tile count as the stride
+// (tiles past the live element count write nothing), and the table size is
+// left in *scan_n for the scan that follows.
 template <int BITS>
 __global__ void __launch_bounds__(RS_THREADS) radix_hist(const uint32_t *keys, int64_t n, const int64_t *n_dev,
-                                                         int shift, uint32_t *counts, int64_t tiles) {
+                                                         int shift, uint32_t *counts, int64_t *scan_n) {
     constexpr int R = 1 << BITS;
     constexpr uint32_t mask = R - 1;
     __shared__ uint32_t h[R];
     if (n_dev) n = min(*n_dev, n);  // never past the launch bound
+    const int64_t live = (n + RS_TILE - 1) / RS_TILE;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *scan_n = live * R;
+    if ((int64_t)blockIdx.x >= live) return;  // block-uniform
     for (int d = threadIdx.x; d < R; d += RS_THREADS) h[d] = 0;
     __syncthreads();
     int64_t base = (int64_t)blockIdx.x * RS_TILE;
@@ -149,7 +155,7 @@ __global__ void __launch_bounds__(RS_THREADS) radix_hist(const uint32_t *keys, i
         if (p < n) atomicAdd(&h[(keys[p] >> shift) & mask], 1u);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < R; d += RS_THREADS) counts[(int64_t)d * tiles + blockIdx.x] = h[d];
+    for (int d = threadIdx.x; d < R; d += RS_THREADS) counts[(int64_t)d * live + blockIdx.x] = h[d];
 }
 
 template <int BITS>
@@ -164,11 +170,12 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter(const uint32_t *__re
     __shared__ uint32_t toff[R];
     if (n_dev) n = min(*n_dev, n);  // never past the launch bound
     if ((int64_t)blockIdx.x * RS_TILE >= n) return;  // tile past the live count (block-uniform)
+    const int64_t live = (n + RS_TILE - 1) / RS_TILE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < R; d += RS_THREADS) {
 #pragma unroll
         for (int w = 0; w < RS_WARPS; ++w) wcnt[w][d] = 0;
-        toff[d] = offs[(int64_t)d * tiles + blockIdx.x];
+        toff[d] = offs[(int64_t)d * live + blockIdx.x];
     }
     __syncthreads();
     const int64_t wbase = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * (32 * RS_ITEMS);
@@ -214,9 +221,10 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter(const uint32_t *__re
 
 template <int BITS>
 void radix_pass(const uint32_t *ka, const uint32_t *va, uint32_t *kb, uint32_t *vb, int64_t n, const int64_t *n_dev,
-                int shift, uint32_t *counts, int64_t tiles, Workspace &ws, cudaStream_t s, cudaError_t *err) {
-    radix_hist<BITS><<<(unsigned)tiles, RS_THREADS, 0, s>>>(ka, n, n_dev, shift, counts, tiles);
-    cudaError_t e = scan_exclusive_impl<uint32_t>(counts, counts, tiles * (1 << BITS), nullptr, ws, s);
+                int shift, uint32_t *counts, int64_t *scan_n, int64_t tiles, Workspace &ws, cudaStream_t s,
+                cudaError_t *err) {
+    radix_hist<BITS><<<(unsigned)tiles, RS_THREADS, 0, s>>>(ka, n, n_dev, shift, counts, scan_n);
+    cudaError_t e = scan_exclusive_impl<uint32_t>(counts, counts, tiles * (1 << BITS), nullptr, ws, s, scan_n);
     if (e != cudaSuccess) {
         *err = e;
         return;
@@ -257,21 +265,22 @@ cudaError_t radix_sort_pairs_dev(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint3
     int64_t tiles = (n + RS_TILE - 1) / RS_TILE;
     size_t mark = ws.used;
     uint32_t *counts = ws.take<uint32_t>((size_t)tiles << width);
-    if (!counts) return cudaErrorMemoryAllocation;
+    int64_t *scan_n = ws.take<int64_t>(1);
+    if (!counts || !scan_n) return cudaErrorMemoryAllocation;
     uint32_t *ka = k0, *va = v0, *kb = k1, *vb = v1;
     cudaError_t err = cudaSuccess;
     for (int shift = 0; shift < nbits; shift += width) {
         switch (width) {
-            case 1: radix_pass<1>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
-            case 2: radix_pass<2>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
-            case 3: radix_pass<3>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
-            case 4: radix_pass<4>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
-            case 5: radix_pass<5>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
-            case 6: radix_pass<6>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
-            case 7: radix_pass<7>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
-            case 8: radix_pass<8>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
-            case 9: radix_pass<9>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
-            default: radix_pass<10>(ka, va, kb, vb, n, n_dev, shift, counts, tiles, ws, s, &err); break;
+            case 1: radix_pass<1>(ka, va, kb, vb, n, n_dev, shift, counts, scan_n, tiles, ws, s, &err); break;
+            case 2: radix_pass<2>(ka, va, kb, vb, n, n_dev, shift, counts, scan_n, tiles, ws, s, &err); break;
+            case 3: radix_pass<3>(ka, va, kb, vb, n, n_dev, shift, counts, scan_n, tiles, ws, s, &err); break;
+            case 4: radix_pass<4>(ka, va, kb, vb, n, n_dev, shift, counts, scan_n, tiles, ws, s, &err); break;
+            case 5: radix_pass<5>(ka, va, kb, vb, n, n_dev, shift, counts, scan_n, tiles, ws, s, &err); break;
+            case 6: radix_pass<6>(ka, va, kb, vb, n, n_dev, shift, counts, scan_n, tiles, ws, s, &err); break;
+            case 7: radix_pass<7>(ka, va, kb, vb, n, n_dev, shift, counts, scan_n, tiles, ws, s, &err); break;
+            case 8: radix_pass<8>(ka, va, kb, vb, n, n_dev, shift, counts, scan_n, tiles, ws, s, &err); break;
+            case 9: radix_pass<9>(ka, va, kb, vb, n, n_dev, shift, counts, scan_n, tiles, ws, s, &err); break;
+            default: radix_pass<10>(ka, va, kb, vb, n, n_dev, shift, counts, scan_n, tiles, ws, s, &err); break;
         }
         if (err != cudaSuccess) return err;
         uint32_t *t = ka; ka = kb; kb = t;
