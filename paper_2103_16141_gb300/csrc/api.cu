@@ -49,7 +49,7 @@ cudaError_t dmalloc(sivf_ctx *c, T **p, size_t n) {
 void free_all(sivf_ctx *c) {
     void *ptrs[] = {c->labels, c->labels_prev, c->own, c->sumv, c->lam, c->lam_prev, c->moving, c->mov_list,
                     c->n_mov_dev, c->snorm, c->snorm_new, c->coff[0], c->coff[1], c->cterm[0], c->cterm[1],
-                    c->cval[0], c->cval[1], c->cclu, c->if_off, c->if_mf0, c->if_cid, c->if_cid16, c->if_pack, c->if_val, c->if_lp,
+                    c->cval[0], c->cval[1], c->cclu, c->if_off, c->if_mf0, c->if_cid, c->if_val, c->sc_off, c->sc_id16, c->sc_id32, c->sc_val, c->sc_pack, c->sc_lp,
                     c->ctr, c->obj_dev, c->ws.base, c->inst_obj, c->inst_k, c->mov_beg, c->clu_koff,
                     c->inst_changed, c->own_row_ptr, c->own_idx, c->own_val, c->clu_doff,
                     c->loop_dev, c->done_dev, c->objf_dev, c->grho};
@@ -78,7 +78,7 @@ void pick_assign_config(sivf_ctx *c) {
     int dev = 0, smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const bool fits = ((size_t)((c->kmax + 3) & ~3) * 4 + (size_t)T * 16) <= (size_t)smem;
+    const bool fits = ((size_t)((c->kmax + 3) & ~3) * 4 + (size_t)T * ASSIGN_STAGE_BYTES) <= (size_t)smem;
     c->assign_global = c->cfg.score_buffer == 2 || (c->cfg.score_buffer == 0 && !fits) ? 1 : 0;
 }
 
@@ -159,6 +159,12 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
         delete c;
         return SIVF_ERR_BAD_CSR;
     }
+    // the scan addresses postings with 32-bit offsets
+    if (2 * nnz + 1024 + 3 * (int64_t)D + IF_PAD >= 0x7FFFFFFFll) {
+        free_all(c);
+        delete c;
+        return SIVF_ERR_INVALID_ARG;
+    }
     c->nnz = nnz;
     c->cap_c = 2 * nnz + 1024;
     const int64_t capc = c->cap_c;
@@ -188,13 +194,24 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
     INIT_CUDA(dmalloc(c, &c->cclu, capc), "alloc");
     INIT_CUDA(dmalloc(c, &c->if_off, (size_t)D + 1), "alloc");
     INIT_CUDA(dmalloc(c, &c->if_mf0, D), "alloc");
-    // posting arrays carry a small tail pad
+    // posting arrays carry a small tail pad; the scan copy also pads every
+    // list to a multiple of 4 entries
     INIT_CUDA(dmalloc(c, &c->if_cid, capc + IF_PAD), "alloc");
-    const bool ids16 = c->kmax <= 65536;
-    if (ids16) INIT_CUDA(dmalloc(c, &c->if_cid16, capc + IF_PAD), "alloc");
     INIT_CUDA(dmalloc(c, &c->if_val, capc + IF_PAD), "alloc");
-    if (c->cfg.prec != SIVF_FP32) INIT_CUDA(dmalloc(c, &c->if_lp, capc + IF_PAD), "alloc");
-    if (c->cfg.prec != SIVF_FP32 && ids16) INIT_CUDA(dmalloc(c, &c->if_pack, capc + IF_PAD), "alloc");
+    c->cap_s = capc + 3 * (int64_t)D + IF_PAD;
+    const size_t caps = (size_t)c->cap_s;
+    const bool ids16 = c->kmax <= 65536;
+    INIT_CUDA(dmalloc(c, &c->sc_off, (size_t)D + 1), "alloc");
+    if (c->cfg.prec == SIVF_FP32) {
+        if (ids16) INIT_CUDA(dmalloc(c, &c->sc_id16, caps), "alloc");
+        else INIT_CUDA(dmalloc(c, &c->sc_id32, caps), "alloc");
+        INIT_CUDA(dmalloc(c, &c->sc_val, caps), "alloc");
+    } else if (ids16) {
+        INIT_CUDA(dmalloc(c, &c->sc_pack, caps), "alloc");
+    } else {
+        INIT_CUDA(dmalloc(c, &c->sc_id32, caps), "alloc");
+        INIT_CUDA(dmalloc(c, &c->sc_lp, caps), "alloc");
+    }
     INIT_CUDA(dmalloc(c, &c->ctr, 1), "alloc");
     INIT_CUDA(dmalloc(c, &c->obj_dev, 2 * (size_t)ni), "alloc");
     INIT_CUDA(cudaMallocHost(reinterpret_cast<void **>(&c->ctr_host), sizeof(DevCounters)), "alloc host");
@@ -221,7 +238,7 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
         // per-cluster arrays; u2 per tuple: 4 sort arrays, term, rank, value,
         // sorted value, 64-bit key, piece sum, unique term and sum (60 B)
         size_t phase1 = 4 * (size_t)N * 4 + 2 * n8 + 14 * k8 + 64 * ((size_t)nnz + 1) + 32 * 4096;
-        size_t phase2 = 16 * ((size_t)capc + 1) + 24 * ((size_t)D + 1) + 16 * 4096;
+        size_t phase2 = 16 * ((size_t)capc + 1) + 32 * ((size_t)D + 1) + 16 * 4096;
         size_t ws = phase1 > phase2 ? phase1 : phase2;
         size_t maxn = (size_t)(capc > N ? capc : N);
         ws += (maxn / 4096 + 2) * 1024 * 4 + (maxn / 2048 + 2) * 16 + 64 * 256 + (1 << 20);

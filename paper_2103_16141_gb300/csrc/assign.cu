@@ -47,11 +47,14 @@ struct AssignParams {
     const float *sumv;
     const int64_t *if_off;
     const int32_t *if_mf0;
-    const int32_t *if_cid;
-    const uint16_t *if_cid16;
-    const uint32_t *if_pack;   // (id << 16) | bf16/fp16 bits, when k <= 65536 and values are 16-bit
+    // scan copy of the inverted file (tiled layout, local ids)
+    const int64_t *sc_off;
+    const uint16_t *sc_id16;
+    const int32_t *sc_id32;
+    const float *sc_val;
+    const uint32_t *sc_pack;   // (id << 16) | bf16/fp16 bits, when k <= 65536 and values are 16-bit
+    const uint16_t *sc_lp;
     uint32_t *grho;            // global score vectors, one kmax slab per CTA (global score-buffer variant)
-    const void *if_vals;
     const int64_t *coff;
     const int32_t *cterm;
     const float *cval;
@@ -73,19 +76,6 @@ struct AssignParams {
     const int32_t *mov_beg;
     unsigned long long *inst_changed;
 };
-
-template <int PREC>
-__device__ __forceinline__ float load_u(const void *p, int pos) {
-    if (PREC == SIVF_FP32) {
-        return __ldg(reinterpret_cast<const float *>(p) + pos);
-    } else if (PREC == SIVF_BF16) {
-        const unsigned short b = __ldg(reinterpret_cast<const unsigned short *>(p) + pos);
-        return __uint_as_float(((unsigned)b) << 16);
-    } else {
-        const unsigned short b = __ldg(reinterpret_cast<const unsigned short *>(p) + pos);
-        return __half2float(__ushort_as_half(b)) * FP16_INV_SCALE;
-    }
-}
 
 // (value, index) ordering: larger value first, then lower index.
 struct Top2 {
@@ -178,28 +168,79 @@ __device__ __forceinline__ int block_inclusive_scan_int(int x, int *warp_s, int 
     return warp_s[warp] + inc;
 }
 
-constexpr int UNR = 8;         // postings per lane per work item
-constexpr int CH = 32 * UNR;   // postings per work item
+constexpr int CH = 2 * SC_BLK;  // postings per work item: two blocks of the tiled layout
 
-// Typed base pointers of the posting arrays and value decoding.
-template <bool CID16>
-__device__ __forceinline__ auto cid_base(const AssignParams &P) {
-    if constexpr (CID16) return P.if_cid16;
-    else return P.if_cid;
+template <int PREC>
+__device__ __forceinline__ float decode_u(unsigned b) {
+    if constexpr (PREC == SIVF_BF16) return __uint_as_float(b << 16);
+    else return __half2float(__ushort_as_half((unsigned short)b)) * FP16_INV_SCALE;
 }
 
-template <int PREC>
-__device__ __forceinline__ auto val_base(const void *p) {
-    if constexpr (PREC == SIVF_FP32) return reinterpret_cast<const float *>(p);
-    else return reinterpret_cast<const unsigned short *>(p);
+// Four postings of one lane: entries 32m + lane (m = 0..3) of a block.
+struct Post4 {
+    int id[4];
+    float u[4];
+};
+
+// One vector load per array of a full block in the tiled layout (block
+// position 4 * lane + m holds entry 32m + lane). pos = list start + block
+// offset + 4 * lane: a multiple of 4 entries, so the loads are aligned.
+template <int PREC, bool CID16>
+__device__ __forceinline__ Post4 load_tiled(const AssignParams &P, int pos) {
+    Post4 r;
+    if constexpr (CID16 && PREC != SIVF_FP32) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(P.sc_pack + pos));
+        const unsigned ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            r.id[m] = (int)(ws[m] >> 16);
+            r.u[m] = decode_u<PREC>(ws[m] & 0xFFFFu);
+        }
+        return r;
+    } else {
+        if constexpr (CID16) {
+            const uint2 w = __ldg(reinterpret_cast<const uint2 *>(P.sc_id16 + pos));
+            r.id[0] = (int)(w.x & 0xFFFFu);
+            r.id[1] = (int)(w.x >> 16);
+            r.id[2] = (int)(w.y & 0xFFFFu);
+            r.id[3] = (int)(w.y >> 16);
+        } else {
+            const int4 w = __ldg(reinterpret_cast<const int4 *>(P.sc_id32 + pos));
+            r.id[0] = w.x;
+            r.id[1] = w.y;
+            r.id[2] = w.z;
+            r.id[3] = w.w;
+        }
+        if constexpr (PREC == SIVF_FP32) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(P.sc_val + pos));
+            r.u[0] = v.x;
+            r.u[1] = v.y;
+            r.u[2] = v.z;
+            r.u[3] = v.w;
+        } else {
+            const uint2 v = __ldg(reinterpret_cast<const uint2 *>(P.sc_lp + pos));
+            r.u[0] = decode_u<PREC>(v.x & 0xFFFFu);
+            r.u[1] = decode_u<PREC>(v.x >> 16);
+            r.u[2] = decode_u<PREC>(v.y & 0xFFFFu);
+            r.u[3] = decode_u<PREC>(v.y >> 16);
+        }
+        return r;
+    }
 }
 
-template <int PREC>
-__device__ __forceinline__ float decode_u(float x) { return x; }
-template <int PREC>
-__device__ __forceinline__ float decode_u(unsigned short b) {
-    if constexpr (PREC == SIVF_BF16) return __uint_as_float(((unsigned)b) << 16);
-    else return __half2float(__ushort_as_half(b)) * FP16_INV_SCALE;
+// One posting at a canonical (tail) position.
+template <int PREC, bool CID16>
+__device__ __forceinline__ void load_one(const AssignParams &P, int pos, int &id, float &u) {
+    if constexpr (CID16 && PREC != SIVF_FP32) {
+        const unsigned w = __ldg(P.sc_pack + pos);
+        id = (int)(w >> 16);
+        u = decode_u<PREC>(w & 0xFFFFu);
+    } else {
+        if constexpr (CID16) id = (int)__ldg(P.sc_id16 + pos);
+        else id = __ldg(P.sc_id32 + pos);
+        if constexpr (PREC == SIVF_FP32) u = __ldg(P.sc_val + pos);
+        else u = decode_u<PREC>((unsigned)__ldg(P.sc_lp + pos));
+    }
 }
 
 // Register budget: resident CTAs per SM at 128 threads (scaled for other
@@ -229,7 +270,6 @@ __device__ __forceinline__ void rho_zero(uint32_t *p) {
 template <int T, int PREC, bool CID16, bool GRHO>
 __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) : 1)
     assign_kernel(AssignParams P) {
-    constexpr bool PACKED = CID16 && PREC != SIVF_FP32;
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int NW = T / 32;
     const int kpad = (P.kmax + 3) & ~3;
@@ -237,7 +277,8 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
     float *s_vs = reinterpret_cast<float *>(GRHO ? smem : smem + kpad);
     int *s_start = reinterpret_cast<int *>(s_vs + T);
     int *s_len = s_start + T;
-    int *s_item = s_len + T;
+    int *s_fb = s_len + T;
+    int *s_item = s_fb + T;
     __shared__ int warp_i[32];
     __shared__ int s_total;
     __shared__ long long s_obj;
@@ -250,7 +291,11 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int j = tid; j < kpad; j += T) rho_zero<GRHO>(rho + j);
-    unsigned long long c_post_obj = 0, c_filt = 0, c_sim = 0, c_resc = 0, c_cand = 0, c_chg = 0;
+    // per-CTA counters in shared memory (written by one thread or by lane 0
+    // of each warp): filtered, sim-calcs, changed, re-scored, re-score candidates
+    __shared__ unsigned long long s_cnt[5];
+    if (tid < 5) s_cnt[tid] = 0ull;
+    unsigned long long c_post_obj = 0;
     __syncthreads();
 
     for (;;) {
@@ -280,22 +325,26 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
         const int32_t *movs = P.mov_list + mb;
 
         // ---- similarity scan (Algorithm 4, lines 7-13) ----
-        // Work items are chunks of CH = 32 * UNR postings of one list
+        // Work items are chunks of CH = 2 blocks of 128 postings of one list
         // (segment), starting at the segment start; only a segment's last chunk
         // can be partial. Warp w takes a contiguous block of the items, so the
-        // owning term (and its start, length and value) changes rarely and
-        // stays in registers. Lane l handles postings l, l+32, ... of a chunk:
-        // coalesced loads, and on dense lists the 32 atomics of one step hit
-        // consecutive ids, i.e. distinct banks.
+        // owning term (and its start, lengths and value) changes rarely and
+        // stays in registers. In a full block of the tiled layout lane l reads
+        // postings l, 32+l, 64+l, 96+l with one vector load per array; step m
+        // of the warp then touches postings 32m .. 32m+31, whose ids are
+        // distinct banks on dense lists. The ragged tail (< 128 postings of a
+        // list) is read one posting per lane and step.
         for (int64_t cb = rb; cb < re; cb += T) {
             const int cn = (int)min((int64_t)T, re - cb);
             int nch = 0;
             if (tid < cn) {
                 const int t = P.idx[cb + tid];
                 const int64_t o0 = P.if_off[t];
-                const int len = filt ? P.if_mf0[t] : (int)(P.if_off[t + 1] - o0);
-                s_start[tid] = (int)o0;
+                const int lfull = (int)(P.if_off[t + 1] - o0);
+                const int len = filt ? P.if_mf0[t] : lfull;
+                s_start[tid] = (int)P.sc_off[t];
                 s_len[tid] = len;
+                s_fb[tid] = lfull & ~(SC_BLK - 1);
                 s_vs[tid] = P.val[cb + tid] * FIX_SCALE;  // exact: power-of-two scaling
                 nch = (len + CH - 1) / CH;
                 c_post_obj += (unsigned long long)len;
@@ -307,68 +356,50 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
             const int per_warp = (items + NW - 1) / NW;
             const int it0 = warp * per_warp;
             const int it1 = min(items, it0 + per_warp);
-            int h = 0, h_first = 0, sb = 0, len = 0;
+            int h = 0, h_first = 0, h_end = 0, sb = 0, len = 0, fb = 0;
             float vs = 0.f;
-            bool have = false;
             for (int it = it0; it < it1; ++it) {
-                if (!have || it >= s_item[h]) {
+                if (it >= h_end) {
                     while (s_item[h] <= it) ++h;
                     h_first = h ? s_item[h - 1] : 0;
+                    h_end = s_item[h];
                     sb = s_start[h];
                     len = s_len[h];
+                    fb = s_fb[h];
                     vs = s_vs[h];
-                    have = true;
                 }
                 const int off = (it - h_first) * CH;  // chunk offset inside the segment
-                const int rem = len - off;            // postings left in the segment
-                if constexpr (PACKED) {
-                    // one 32-bit word per posting: id in the high half, value in the low half
-                    const uint32_t *pw = P.if_pack + (sb + off + lane);
-                    uint32_t ww[UNR];
-                    if (rem >= CH) {
+                if (off + CH <= len && off + CH <= fb) {
+                    // two full blocks, every posting scanned
+                    const Post4 a = load_tiled<PREC, CID16>(P, sb + off + 4 * lane);
+                    const Post4 b = load_tiled<PREC, CID16>(P, sb + off + SC_BLK + 4 * lane);
 #pragma unroll
-                        for (int m = 0; m < UNR; ++m) ww[m] = __ldg(pw + 32 * m);
+                    for (int m = 0; m < 4; ++m) atomicAdd(&rho[a.id[m]], __float2uint_ru(vs * a.u[m]));
 #pragma unroll
-                        for (int m = 0; m < UNR; ++m)
-                            atomicAdd(&rho[ww[m] >> 16],
-                                      __float2uint_ru(vs * decode_u<PREC>((unsigned short)(ww[m] & 0xFFFFu))));
-                    } else {
-#pragma unroll
-                        for (int m = 0; m < UNR; ++m)
-                            if (32 * m + lane < rem) ww[m] = __ldg(pw + 32 * m);
-#pragma unroll
-                        for (int m = 0; m < UNR; ++m)
-                            if (32 * m + lane < rem)
-                                atomicAdd(&rho[ww[m] >> 16],
-                                          __float2uint_ru(vs * decode_u<PREC>((unsigned short)(ww[m] & 0xFFFFu))));
-                    }
+                    for (int m = 0; m < 4; ++m) atomicAdd(&rho[b.id[m]], __float2uint_ru(vs * b.u[m]));
                     continue;
                 }
-                const auto *pc = cid_base<CID16>(P) + (sb + off + lane);
-                const auto *pv = val_base<PREC>(P.if_vals) + (sb + off + lane);
-                if (rem >= CH) {
-                    int cc[UNR];
-                    float uu[UNR];
 #pragma unroll
-                    for (int m = 0; m < UNR; ++m) {
-                        cc[m] = (int)__ldg(pc + 32 * m) - (CID16 ? 0 : k_off);
-                        uu[m] = decode_u<PREC>(__ldg(pv + 32 * m));
+                for (int bi = 0; bi < 2; ++bi) {
+                    const int bo = off + bi * SC_BLK;
+                    if (bo >= len) break;
+                    if (bo < fb) {
+                        // a full block of the list (the loads stay inside it),
+                        // of which the front part may end inside
+                        const Post4 a = load_tiled<PREC, CID16>(P, sb + bo + 4 * lane);
+#pragma unroll
+                        for (int m = 0; m < 4; ++m)
+                            if (bo + 32 * m + lane < len) atomicAdd(&rho[a.id[m]], __float2uint_ru(vs * a.u[m]));
+                    } else {
+                        int id[4];
+                        float u[4];
+#pragma unroll
+                        for (int m = 0; m < 4; ++m)
+                            if (bo + 32 * m + lane < len) load_one<PREC, CID16>(P, sb + bo + 32 * m + lane, id[m], u[m]);
+#pragma unroll
+                        for (int m = 0; m < 4; ++m)
+                            if (bo + 32 * m + lane < len) atomicAdd(&rho[id[m]], __float2uint_ru(vs * u[m]));
                     }
-#pragma unroll
-                    for (int m = 0; m < UNR; ++m) atomicAdd(&rho[cc[m]], __float2uint_ru(vs * uu[m]));
-                } else {
-                    int cc[UNR];
-                    float uu[UNR];
-#pragma unroll
-                    for (int m = 0; m < UNR; ++m) {
-                        if (32 * m + lane < rem) {
-                            cc[m] = (int)__ldg(pc + 32 * m) - (CID16 ? 0 : k_off);
-                            uu[m] = decode_u<PREC>(__ldg(pv + 32 * m));
-                        }
-                    }
-#pragma unroll
-                    for (int m = 0; m < UNR; ++m)
-                        if (32 * m + lane < rem) atomicAdd(&rho[cc[m]], __float2uint_ru(vs * uu[m]));
                 }
             }
             __syncthreads();
@@ -452,7 +483,7 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
             if (lane == 0) {
                 warp_d[warp] = wbest;
                 warp_j[warp] = wj;
-                c_cand += (unsigned long long)ncand;
+                if (ncand) atomicAdd(&s_cnt[4], (unsigned long long)ncand);
             }
             __syncthreads();
             if (tid == 0) {
@@ -465,7 +496,7 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
                     }
                 }
                 if (bj != INT32_MAX) s_winner = bj;
-                c_resc += 1;
+                s_cnt[3] += 1;
             }
             __syncthreads();
         }
@@ -477,13 +508,13 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
             P.labels[i] = a;
             P.own[i] = (filt && al == a_loc) ? own_q : rho_ld<GRHO>(rho + al);
             if (a != a_prev) {
-                c_chg += 1;
+                s_cnt[2] += 1;
                 P.moving[a] = 1;
                 if (a_prev >= 0) P.moving[a_prev] = 1;
                 if (P.n_inst > 1) atomicAdd(P.inst_changed + inst, 1ull);
             }
-            c_filt += filt ? 1ull : 0ull;
-            c_sim += filt ? (unsigned long long)n_mov : (unsigned long long)km;
+            s_cnt[0] += filt ? 1ull : 0ull;
+            s_cnt[1] += filt ? (unsigned long long)n_mov : (unsigned long long)km;
         }
         __syncthreads();
         if (!filt) {
@@ -498,14 +529,15 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c_post_obj += __shfl_xor_sync(0xffffffffu, c_post_obj, o);
     if (lane == 0 && c_post_obj) atomicAdd(&P.ctr->postings, c_post_obj);
+    __syncthreads();
     if (tid == 0) {
-        atomicAdd(&P.ctr->filtered, c_filt);
-        atomicAdd(&P.ctr->simcalc, c_sim);
-        atomicAdd(&P.ctr->changed, c_chg);
-    }
-    if (lane == 0 && (c_resc | c_cand)) {
-        atomicAdd(&P.ctr->rescored, c_resc);
-        atomicAdd(&P.ctr->rescore_cands, c_cand);
+        atomicAdd(&P.ctr->filtered, s_cnt[0]);
+        atomicAdd(&P.ctr->simcalc, s_cnt[1]);
+        atomicAdd(&P.ctr->changed, s_cnt[2]);
+        if (s_cnt[3] | s_cnt[4]) {
+            atomicAdd(&P.ctr->rescored, s_cnt[3]);
+            atomicAdd(&P.ctr->rescore_cands, s_cnt[4]);
+        }
     }
 }
 
@@ -549,7 +581,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(int32_t k, int first_ite
 template <int T, int PREC, bool CID16, bool GRHO>
 cudaError_t launch_t(sivf_ctx *c, const AssignParams &P, int ctas_per_sm) {
     const int kpad = (c->kmax + 3) & ~3;
-    const size_t smem = (GRHO ? 0 : (size_t)kpad * 4) + (size_t)T * 16;
+    const size_t smem = (GRHO ? 0 : (size_t)kpad * 4) + (size_t)T * ASSIGN_STAGE_BYTES;
     auto kern = assign_kernel<T, PREC, CID16, GRHO>;
     // the attribute and occupancy queries are host calls that a stream capture
     // refuses: they run on the first (host-launched) step and are cached
@@ -581,9 +613,10 @@ cudaError_t launch_prec(sivf_ctx *c, const AssignParams &P) {
 
 template <int PREC>
 cudaError_t launch_ids(sivf_ctx *c, const AssignParams &P) {
+    const bool ids16 = P.sc_id16 || P.sc_pack;
     if (c->assign_global)
-        return P.if_cid16 ? launch_prec<PREC, true, true>(c, P) : launch_prec<PREC, false, true>(c, P);
-    return P.if_cid16 ? launch_prec<PREC, true, false>(c, P) : launch_prec<PREC, false, false>(c, P);
+        return ids16 ? launch_prec<PREC, true, true>(c, P) : launch_prec<PREC, false, true>(c, P);
+    return ids16 ? launch_prec<PREC, true, false>(c, P) : launch_prec<PREC, false, false>(c, P);
 }
 
 }  // namespace
@@ -599,11 +632,13 @@ cudaError_t launch_assign(sivf_ctx *c) {
     P.sumv = c->sumv;
     P.if_off = c->if_off;
     P.if_mf0 = c->if_mf0;
-    P.if_cid = c->if_cid;
-    P.if_cid16 = c->if_cid16;
-    P.if_pack = c->if_pack;
+    P.sc_off = c->sc_off;
+    P.sc_id16 = c->sc_id16;
+    P.sc_id32 = c->sc_id32;
+    P.sc_val = c->sc_val;
+    P.sc_pack = c->sc_pack;
+    P.sc_lp = c->sc_lp;
     P.grho = c->grho;
-    P.if_vals = c->cfg.prec == SIVF_FP32 ? (const void *)c->if_val : (const void *)c->if_lp;
     P.coff = c->coff[c->cur];
     P.cterm = c->cterm[c->cur];
     P.cval = c->cval[c->cur];
@@ -665,7 +700,7 @@ cudaError_t autotune_assign(sivf_ctx *c) {
     for (int g = 0; g < 2; ++g) {
         if (g == 1 && !c->grho) continue;
         for (int t : threads) {
-            if (!g && (size_t)kpad * 4 + (size_t)t * 16 > (size_t)dev_smem) continue;
+            if (!g && (size_t)kpad * 4 + (size_t)t * ASSIGN_STAGE_BYTES > (size_t)dev_smem) continue;
             float trial = 1e30f;
             for (int rep = 0; rep < 2; ++rep) {  // best of two launches
             SIVF_CUDA_TRY(cudaMemcpyAsync(c->own, own_snap, sizeof(uint32_t) * c->N, cudaMemcpyDeviceToDevice, s));

@@ -12,9 +12,18 @@
 //                                        cluster-major FP32 master copy, ascending terms
 //   snorm                 f64[k]        ||s_j|| of the sum behind each centroid
 //   inverted file         if_off int64[D+1], if_mf0 int32[D], if_cid int32[cap],
-//                                        if_cid16 u16[cap] (k <= 65536), if_val f32[cap],
-//                                        if_lp u16[cap] (bf16/fp16 copy), if_pack u32[cap]
-//                                        (id << 16 | bf16/fp16 value, read by the scan)
+//                                        if_val f32[cap]: canonical order (front ids
+//                                        ascending, then back ids ascending)
+//   scan copy of the file sc_off int64[D+1]: each list starts at a multiple of 4
+//                                        entries; a list's full 128-entry blocks are
+//                                        stored transposed (entry 32m + l of a block at
+//                                        block position 4l + m), so that lane l reads
+//                                        entries l, 32+l, 64+l, 96+l with one vector
+//                                        load; the ragged tail keeps canonical order.
+//                                        Arrays (local cluster ids): sc_id16 u16 or
+//                                        sc_id32 int32, plus sc_val f32 (FP32), or
+//                                        sc_pack u32 = id << 16 | bf16/fp16 value
+//                                        (16-bit ids and values), or sc_lp u16
 #pragma once
 
 #include <cuda_runtime.h>
@@ -30,6 +39,11 @@ namespace sivf {
 constexpr uint32_t OWN_INVALID = 0xFFFFFFFFu;
 // tail padding (entries) of the inverted-file posting arrays
 constexpr int64_t IF_PAD = 256;
+// block of the tiled scan layout: 32 lanes x 4 entries
+constexpr int SC_BLK = 128;
+// shared memory the assignment kernel stages per thread besides the score
+// vector: list start, scanned length, full-block end, scaled value, item prefix
+constexpr int ASSIGN_STAGE_BYTES = 20;
 // Scores are accumulated as unsigned fixed point with quantum 2^-31:
 // q = ceil(fl(v * u) * 2^31). Cosine scores are <= 1 (+ rounding), so the
 // sum of an object's terms stays below 2^32.
@@ -113,11 +127,17 @@ struct sivf_ctx {
     int64_t *if_off = nullptr;
     int32_t *if_mf0 = nullptr;
     int32_t *if_cid = nullptr;
-    uint16_t *if_cid16 = nullptr;  // 16-bit copy of if_cid when k <= 65536 (read by the scan)
-    uint32_t *if_pack = nullptr;   // (id << 16) | 16-bit value, for bf16/fp16 postings when k <= 65536
     float *if_val = nullptr;
-    uint16_t *if_lp = nullptr;
     int64_t if_nnz = 0;
+    // scan copy (tiled layout, local ids); which arrays exist depends on the
+    // id width (16 bits when every instance has k <= 65536) and the precision
+    int64_t *sc_off = nullptr;
+    uint16_t *sc_id16 = nullptr;
+    int32_t *sc_id32 = nullptr;
+    float *sc_val = nullptr;      // FP32 postings
+    uint32_t *sc_pack = nullptr;  // 16-bit ids and 16-bit values
+    uint16_t *sc_lp = nullptr;    // 32-bit ids and 16-bit values
+    int64_t cap_s = 0;            // entries of each scan array
 
     // counters and step scratch
     sivf::DevCounters *ctr = nullptr;

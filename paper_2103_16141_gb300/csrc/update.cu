@@ -446,19 +446,31 @@ __global__ void k_if_keys(const int64_t *n_dev, int64_t cap, const int32_t *cter
     }
 }
 
-__global__ void k_if_lens(int32_t D, const uint32_t *cnt2, int64_t *len, int32_t *mf0) {
+__global__ void k_if_lens(int32_t D, const uint32_t *cnt2, int64_t *len, int64_t *slen, int32_t *mf0) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < D) {
-        len[t] = (int64_t)cnt2[2 * t] + (int64_t)cnt2[2 * t + 1];
+        const int64_t l = (int64_t)cnt2[2 * t] + (int64_t)cnt2[2 * t + 1];
+        len[t] = l;
+        slen[t] = (l + 3) & ~(int64_t)3;  // scan copy: lists start at multiples of 4 entries
         mf0[t] = (int32_t)cnt2[2 * t];
     }
 }
 
-// if_cid holds global cluster ids; the scan arrays (if_cid16, if_pack) hold
-// ids local to the cluster's instance.
-__global__ void k_if_fill(const int64_t *n_dev, int64_t cap, const uint32_t *order, const int32_t *cclu,
-                          const int32_t *clu_koff, const float *cval, int prec, int32_t *if_cid, uint16_t *if_cid16,
-                          uint32_t *if_pack, float *if_val, uint16_t *if_lp) {
+// Position of entry p of a list of length L in the tiled scan layout: inside
+// the list's full 128-entry blocks, entry 32m + l of a block sits at block
+// position 4l + m; the ragged tail keeps canonical order.
+__device__ __forceinline__ int64_t tiled_pos(int64_t p, int64_t L) {
+    const int64_t fb = L & ~(int64_t)(SC_BLK - 1);
+    if (p >= fb) return p;
+    return (p & ~(int64_t)(SC_BLK - 1)) | ((p & 31) << 2) | ((p >> 5) & 3);
+}
+
+// Canonical arrays (if_cid: global cluster ids, if_val) in sorted order, and
+// the scan copy (local ids) at its tiled positions.
+__global__ void k_if_fill(const int64_t *n_dev, int64_t cap, const uint32_t *order, const uint32_t *skeys,
+                          const int64_t *if_off, const int64_t *sc_off, const int32_t *cclu, const int32_t *clu_koff,
+                          const float *cval, int prec, int32_t *if_cid, float *if_val, uint16_t *sc_id16,
+                          int32_t *sc_id32, float *sc_val, uint32_t *sc_pack, uint16_t *sc_lp) {
     const int64_t n = min(*n_dev, cap);
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t e = order[q];
@@ -466,18 +478,25 @@ __global__ void k_if_fill(const int64_t *n_dev, int64_t cap, const uint32_t *ord
         const int32_t j = cclu[e];
         const uint32_t jl = (uint32_t)(j - clu_koff[j]);
         if_cid[q] = j;
-        if (if_cid16) if_cid16[q] = (uint16_t)jl;
         if_val[q] = u;
-        unsigned short lp = 0;
+        const uint32_t t = skeys[q] >> 1;
+        const int64_t o = if_off[t];
+        const int64_t s = sc_off[t] + tiled_pos(q - o, if_off[t + 1] - o);
+        if (sc_id16) sc_id16[s] = (uint16_t)jl;
+        if (sc_id32) sc_id32[s] = (int32_t)jl;
+        if (prec == SIVF_FP32) {
+            sc_val[s] = u;
+            continue;
+        }
+        unsigned short lp;
         if (prec == SIVF_BF16) {
             lp = __bfloat16_as_ushort(__float2bfloat16_rn(u));
-            if_lp[q] = lp;
-        } else if (prec == SIVF_FP16) {
+        } else {
             lp = __half_as_ushort(__float2half_rn(u * FP16_SCALE));
             if (lp == 0 && u > 0.0f) lp = 1;  // keep every posting strictly positive
-            if_lp[q] = lp;
         }
-        if (if_pack) if_pack[q] = (jl << 16) | (uint32_t)lp;
+        if (sc_pack) sc_pack[s] = (jl << 16) | (uint32_t)lp;
+        else sc_lp[s] = lp;
     }
 }
 
@@ -573,22 +592,26 @@ cudaError_t build_inverted_file(sivf_ctx *c) {
     size_t mark = ws.used;
     uint32_t *cnt2 = ws.take<uint32_t>((size_t)2 * c->D);
     int64_t *len = ws.take<int64_t>((size_t)c->D + 1);
-    int64_t *total = ws.take<int64_t>(1);
+    int64_t *slen = ws.take<int64_t>((size_t)c->D + 1);
+    int64_t *total = ws.take<int64_t>(2);
     uint32_t *k0 = ws.take<uint32_t>((size_t)cap + 1), *v0 = ws.take<uint32_t>((size_t)cap + 1);
     uint32_t *k1 = ws.take<uint32_t>((size_t)cap + 1), *v1 = ws.take<uint32_t>((size_t)cap + 1);
-    if (!cnt2 || !len || !total || !k0 || !v0 || !k1 || !v1) return cudaErrorMemoryAllocation;
+    if (!cnt2 || !len || !slen || !total || !k0 || !v0 || !k1 || !v1) return cudaErrorMemoryAllocation;
     SIVF_CUDA_TRY(cudaMemsetAsync(cnt2, 0, sizeof(uint32_t) * 2 * c->D, c->stream));
     k_if_keys<<<blocks_for(cap), TPB, 0, c->stream>>>(n_dev, cap, c->cterm[cur], c->cclu, c->lam, k0, v0, cnt2);
-    k_if_lens<<<blocks_for(c->D), TPB, 0, c->stream>>>(c->D, cnt2, len, c->if_mf0);
+    k_if_lens<<<blocks_for(c->D), TPB, 0, c->stream>>>(c->D, cnt2, len, slen, c->if_mf0);
     note_launch(2);
     SIVF_CUDA_TRY(cudaGetLastError());
     SIVF_CUDA_TRY(scan_exclusive_i64(len, c->if_off, c->D, total, ws, c->stream));
     SIVF_CUDA_TRY(cudaMemcpyAsync(c->if_off + c->D, total, sizeof(int64_t), cudaMemcpyDeviceToDevice, c->stream));
+    SIVF_CUDA_TRY(scan_exclusive_i64(slen, c->sc_off, c->D, total + 1, ws, c->stream));
+    SIVF_CUDA_TRY(cudaMemcpyAsync(c->sc_off + c->D, total + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, c->stream));
     bool alt = false;
     SIVF_CUDA_TRY(radix_sort_pairs_dev(k0, v0, k1, v1, cap, n_dev, c->bits_t + 1, &alt, ws, c->stream));
-    k_if_fill<<<blocks_for(cap), TPB, 0, c->stream>>>(n_dev, cap, alt ? v1 : v0, c->cclu, c->clu_koff, c->cval[cur],
-                                                      (int)c->cfg.prec, c->if_cid, c->if_cid16, c->if_pack, c->if_val,
-                                                      c->if_lp);
+    k_if_fill<<<blocks_for(cap), TPB, 0, c->stream>>>(n_dev, cap, alt ? v1 : v0, alt ? k1 : k0, c->if_off, c->sc_off,
+                                                      c->cclu, c->clu_koff, c->cval[cur], (int)c->cfg.prec, c->if_cid,
+                                                      c->if_val, c->sc_id16, c->sc_id32, c->sc_val, c->sc_pack,
+                                                      c->sc_lp);
     note_launch();
     SIVF_CUDA_TRY(cudaGetLastError());
     ws.used = mark;

@@ -35,6 +35,18 @@ def test_mid_lockstep_block_sizes(threads):
     lockstep(c, w.k, ini, 8, threads=threads)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
+def test_long_lists_tiled_blocks(precision):
+    """Posting lists of up to three full 128-entry blocks plus a ragged tail
+    (a 1,500-term vocabulary shared by k = 500 centroids), with ICP fronts
+    longer than one block that end inside a full block (iterations 3-6): the
+    tiled scan layout against the oracle."""
+    w = CONFIGS["c2"].scaled(N=8_000, D=1_500, k=500, mu=3.5, hi=400)
+    c, ini = corpus_for(w, seed=31)
+    recs = lockstep(c, w.k, ini, 10, precision=precision)
+    assert any(r["stats"]["filtered"] > 0 for r in recs)
+
+
 def test_free_running_c1_matches_oracle_every_iteration():
     w = CONFIGS["c1"]
     c, ini = corpus_for(w)
