@@ -73,7 +73,7 @@ def recorded_traffic(w):
         return None, None
     if rec.get("source_sha256") != sha:
         return None, None
-    return float(rec["dram_bytes_per_launch"]), rec.get("launch")
+    return float(rec["dram_bytes_per_launch"]), rec
 
 
 def load_peaks():
@@ -382,18 +382,26 @@ def main():
         kernel_times_from = "one host-stepped run of the same workload (graph replay hides per-launch times)"
     hbm_peak, peak_src = load_peaks()
     b_post = (B_POST16 if w.k <= 65536 else B_POST32)[w.precision]
-    alg_bytes = sum(c.nnz * 8 + (w.N + 1) * 8 + p["postings"] * b_post + w.N * 16 + w.k for p in all_per)
+    fixed = c.nnz * 8 + (w.N + 1) * 8 + w.N * 16 + w.k
+    alg_bytes = sum(fixed + p["postings"] * b_post for p in all_per)
+    # compulsory bytes: every posting of the scanned file read once (the file
+    # of iteration r is built by update r-1; the first one holds the seed rows)
+    seed_nnz = int(sum(c.row_ptr[i + 1] - c.row_ptr[i] for i in ini))
+    if_nnz = [seed_nnz] + [p.get("centroid_nnz", 0) for p in all_per[:-1]]
+    min_bytes = sum(fixed + n * b_post for n in if_nnz)
     ms_assign = sum(p["ms_assign"] for p in all_per)
     ms_update = sum(p.get("ms_update", 0.0) for p in all_per)
     stepped_iters = len(all_per)
     achieved = alg_bytes / (ms_assign / 1e3) / 1e9 if ms_assign > 0 else 0.0
     postings = sum(p["postings"] for p in all_per)
+    simcalc = sum(p["simcalc"] for p in all_per)
     iters_per_step = tot_iters / args.steps
-    traffic, traffic_launch = recorded_traffic(w)
+    traffic, trec = recorded_traffic(w)
 
     # end to end: host corpus in pinned memory -> device, init, run, labels back
     e2e = None
     if not args.no_e2e:
+        # the C ABI copies the pinned host CSR itself (inputs_on_host)
         rp = torch.from_numpy(c.row_ptr).pin_memory()
         ix = torch.from_numpy(c.idx).pin_memory()
         vl = torch.from_numpy(c.val).pin_memory()
@@ -405,12 +413,9 @@ def main():
         e_iters = 0
         E = max(1, min(args.steps, 3))
         for _ in range(E):
-            d_rp = rp.to(dev, non_blocking=True)
-            d_ix = ix.to(dev, non_blocking=True)
-            d_vl = vl.to(dev, non_blocking=True)
-            ge = SIVF(d_rp, d_ix, d_vl, c.D, w.k, ini, precision=w.precision, icp=bool(args.icp),
+            ge = SIVF(rp, ix, vl, c.D, w.k, ini, precision=w.precision, icp=bool(args.icp),
                       threads=args.threads, ctas_per_sm=args.ctas_per_sm, use_graph=bool(args.graph),
-             autotune=bool(args.autotune))
+                      autotune=bool(args.autotune), inputs_on_host=True)
             it, _ = ge.run(w.max_iter)
             e_iters += it
             S.sivf_get_labels(ge.ctx, lab_host.data_ptr(), False)
@@ -435,20 +440,32 @@ def main():
                                    f"len=lognormal({w.mu:.3f},{w.sigma}) clip[{w.lo},{w.hi}] seed={w.seed}",
                        "precision": w.precision, "icp": bool(args.icp), "max_iter": w.max_iter,
                        "iters_per_step": iters_per_step, "sec_per_iter": ms / 1e3 / tot_iters,
-                       "l2": "inputs larger than L2 (CSR 0.46 GB; inverted file > 129 MB)",
+                       "l2": f"inputs larger than L2: every assignment streams the object CSR "
+                             f"({(c.nnz * 8 + (w.N + 1) * 8) / 1e9:.2f} GB); the inverted file is reused from L2 "
+                             f"within a launch",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "cuda_graph": bool(args.graph), "autotune": bool(args.autotune),
                        "assign_threads": g.stats()["assign_threads"],
                        "score_buffer": "global" if g.stats()["assign_global"] else "shared"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": traffic, "traffic_launch": traffic_launch,
+                         "frac": achieved / hbm_peak, "traffic": traffic,
+                         "traffic_launch": trec.get("launch") if trec else None,
                          "peak_source": peak_src, "kernel": "assign_kernel",
-                         "bytes_model": "nnz*8 + (N+1)*8 + postings*b_post + N*16 + k (no cache credit)",
-                         "note": "posting bytes are served by L2 (ncu: 94% L2 hit, DRAM bytes = traffic); "
-                                 "frac > 1 means on-chip reuse, see profiles/",
+                         "bytes_model": f"nnz*8 + (N+1)*8 + postings*b_post + N*16 + k, b_post = {b_post} B "
+                                        f"(no cache credit)",
+                         "note": "posting bytes are served by L2, not HBM (traffic = ncu DRAM bytes of one "
+                                 "launch); frac > 1 means on-chip reuse, see profiles/",
+                         "compulsory_frac": min_bytes / (ms_assign / 1e3) / 1e9 / hbm_peak if ms_assign > 0 else None,
+                         "ncu_dram_gbs": (traffic / trec["ncu_duration_s"] / 1e9) if trec else None,
                          "postings_per_s": postings / (ms_assign / 1e3) if ms_assign > 0 else None,
+                         "simcalc_ratio": simcalc / (float(w.N) * w.k * stepped_iters),
                          "ms_assign_per_iter": ms_assign / stepped_iters, "ms_update_per_iter": ms_update / stepped_iters,
                          "kernel_times_from": kernel_times_from},
+            "per_iteration": {"postings": [int(p["postings"]) for p in all_per[:60]],
+                              "filtered": [int(p["filtered"]) for p in all_per[:60]],
+                              "rescored": [int(p["rescored"]) for p in all_per[:60]],
+                              "ms_assign": [round(p["ms_assign"], 3) for p in all_per[:60]],
+                              "ms_update": [round(p.get("ms_update", 0.0), 3) for p in all_per[:60]]},
             "gpu_launches": int(launches),
             "clocks": clocks,
         }

@@ -54,7 +54,8 @@ typedef enum { SIVF_FP32 = 0, SIVF_BF16 = 1, SIVF_FP16 = 2 } sivf_precision;
 typedef struct {
     sivf_precision prec; /* posting value precision for the scan */
     int icp;             /* 1: ICP filter (Algorithm 4); 0: unfiltered (Algorithm 2) */
-    int threads;         /* threads per CTA of the assignment kernel; 0 = automatic */
+    int threads;         /* threads per CTA of the assignment kernel (32, 64, 128, 256 or
+                            512); 0 = automatic */
     int ctas_per_sm;     /* resident CTAs per SM of the assignment kernel; 0 = automatic */
     int64_t mem_cap_bytes; /* cap on library-owned device memory; 0 = no cap */
     int use_graph;       /* 1: after the first two iterations, sivf_run / sivf_batch_run
@@ -64,8 +65,16 @@ typedef struct {
     int autotune;        /* 1: at the second assignment, time every feasible assignment
                             kernel configuration (threads per CTA x score vector in shared
                             or global memory) on the live state and keep the fastest;
-                            threads / ctas_per_sm then only seed the search */
+                            threads / ctas_per_sm then only seed the search. The choice
+                            is remembered for the process (per device and problem
+                            shape), so later contexts of the same shape skip the trials */
     int score_buffer;    /* 0: automatic (shared memory when k fits), 1: shared, 2: global */
+    int inputs_on_host;  /* sivf_init only. 1: row_ptr / idx / val are HOST memory; the
+                            library copies them (on the stream, asynchronously when the host
+                            memory is pinned) into device buffers it owns and frees in
+                            sivf_destroy, and the host arrays may be released once
+                            sivf_init returns. 0: DEVICE memory, borrowed. sivf_batch_init
+                            rejects 1 (its descriptors are DEVICE). */
 } sivf_config;
 
 /* Counters of the most recent assignment / update (host copy). */
@@ -104,10 +113,13 @@ typedef struct sivf_ctx sivf_ctx; /* opaque, library-owned */
  *   idx      : DEVICE int32[nnz], term ids in [0, D), strictly ascending in each row.
  *   val      : DEVICE float[nnz], tf-idf values > 0, each row of unit L2 norm.
  *              row_ptr / idx / val are BORROWED: they must stay valid and
- *              unchanged until sivf_destroy.
+ *              unchanged until sivf_destroy. With cfg->inputs_on_host = 1 all
+ *              three are HOST arrays instead, copied at init.
  *   init_ids : HOST int32[k], distinct object ids; mu_j^[0] = x_{init_ids[j]}. Copied.
  *   stream   : cudaStream_t (may be NULL = legacy default stream).
- * Errors: SIVF_ERR_INVALID_ARG (sizes, ids), SIVF_ERR_BAD_CSR (row_ptr not
+ * Errors: SIVF_ERR_INVALID_ARG (sizes, ids; 2 nnz + 3 D + 1280 must stay
+ * below 2^31 - 1, the range of the scan's 32-bit posting offsets),
+ * SIVF_ERR_BAD_CSR (row_ptr not
  * monotone, idx out of range or not ascending, val not finite and positive,
  * a row norm off 1 by more than 1e-4), SIVF_ERR_OOM, SIVF_ERR_CUDA.
  */

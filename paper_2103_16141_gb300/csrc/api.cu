@@ -71,7 +71,7 @@ sivf_status check_usable(sivf_ctx *c) {
 
 void pick_assign_config(sivf_ctx *c) {
     int T = c->cfg.threads;
-    if (T != 64 && T != 128 && T != 256 && T != 512) T = 0;
+    if (T != 32 && T != 64 && T != 128 && T != 256 && T != 512) T = 0;
     if (T == 0) T = c->kmax <= 256 ? 64 : (c->kmax <= 4096 ? 128 : 512);
     c->assign_threads = T;
     c->assign_ctas_per_sm = c->cfg.ctas_per_sm > 0 ? c->cfg.ctas_per_sm : 0;
@@ -331,6 +331,37 @@ sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t
         return SIVF_ERR_INVALID_ARG;
     if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16)) return SIVF_ERR_INVALID_ARG;
     if (!distinct_ids(init_ids, k, N)) return SIVF_ERR_INVALID_ARG;
+    if (cfg && cfg->inputs_on_host) {
+        // host CSR: copy it into device buffers that the context adopts
+        const int64_t nnz = row_ptr[N];
+        if (row_ptr[0] != 0 || nnz < 0 || nnz >= 0x7FFFFFFFll) return SIVF_ERR_BAD_CSR;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        int64_t *rp = nullptr;
+        int32_t *ix = nullptr;
+        float *vl = nullptr;
+        const size_t nz = nnz > 0 ? (size_t)nnz : 1;
+        if (cudaMalloc(reinterpret_cast<void **>(&rp), sizeof(int64_t) * (size_t)(N + 1)) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void **>(&ix), sizeof(int32_t) * nz) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void **>(&vl), sizeof(float) * nz) != cudaSuccess) {
+            cudaFree(rp);
+            cudaFree(ix);
+            cudaFree(vl);
+            cudaGetLastError();
+            return SIVF_ERR_OOM;
+        }
+        if (cudaMemcpyAsync(rp, row_ptr, sizeof(int64_t) * (size_t)(N + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            (nnz > 0 && cudaMemcpyAsync(ix, idx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+            (nnz > 0 && cudaMemcpyAsync(vl, val, sizeof(float) * (size_t)nnz, cudaMemcpyHostToDevice, s) != cudaSuccess)) {
+            cudaStreamSynchronize(s);
+            cudaFree(rp);
+            cudaFree(ix);
+            cudaFree(vl);
+            return SIVF_ERR_CUDA;
+        }
+        // create_ctx synchronises the stream before it returns, so the host
+        // arrays are no longer read once this call returns
+        return create_ctx(out, cfg, N, D, k, rp, ix, vl, init_ids, stream, {0, N}, {0, k}, {0, D}, rp, ix, vl);
+    }
     return create_ctx(out, cfg, N, D, k, row_ptr, idx, val, init_ids, stream, {0, N}, {0, k}, {0, D}, nullptr,
                       nullptr, nullptr);
 }
@@ -340,7 +371,7 @@ sivf_status sivf_batch_init(sivf_ctx **out, const sivf_config *cfg, int32_t n_in
     if (!out) return SIVF_ERR_INVALID_ARG;
     *out = nullptr;
     if (n_inst < 1 || n_inst > 65536 || !descs) return SIVF_ERR_INVALID_ARG;
-    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16)) return SIVF_ERR_INVALID_ARG;
+    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16 || cfg->inputs_on_host)) return SIVF_ERR_INVALID_ARG;
     std::vector<int64_t> inst_obj(1, 0);
     std::vector<int32_t> inst_k(1, 0), inst_d(1, 0);
     for (int32_t m = 0; m < n_inst; ++m) {

@@ -32,6 +32,12 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
 #include "sivf_internal.cuh"
 
 namespace sivf {
@@ -168,7 +174,63 @@ __device__ __forceinline__ int block_inclusive_scan_int(int x, int *warp_s, int 
     return warp_s[warp] + inc;
 }
 
-constexpr int CH = 2 * SC_BLK;  // postings per work item: two blocks of the tiled layout
+// Inclusive scan of an (x, y) pair over the block (both components at once).
+template <int T>
+__device__ __forceinline__ int2 block_inclusive_scan_int2(int2 v, int2 *warp_s, int2 *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int2 inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, inc.x, o);
+        const int b = __shfl_up_sync(0xffffffffu, inc.y, o);
+        if (lane >= o) {
+            inc.x += a;
+            inc.y += b;
+        }
+    }
+    if (lane == 31) warp_s[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        constexpr int NW = T / 32;
+        const int2 w = lane < NW ? warp_s[lane] : make_int2(0, 0);
+        int2 winc = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int a = __shfl_up_sync(0xffffffffu, winc.x, o);
+            const int b = __shfl_up_sync(0xffffffffu, winc.y, o);
+            if (lane >= o) {
+                winc.x += a;
+                winc.y += b;
+            }
+        }
+        if (lane < NW) warp_s[lane] = make_int2(winc.x - w.x, winc.y - w.y);
+        if (lane == NW - 1) *total = winc;
+    }
+    __syncthreads();
+    const int2 base = warp_s[warp];
+    return make_int2(base.x + inc.x, base.y + inc.y);
+}
+
+// First index h in [0, T) with a[h] > x, for an ascending array whose last
+// entry exceeds x.
+template <int T>
+__device__ __forceinline__ int first_greater(const int *a, int x) {
+    int lo = 0, hi = T - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] > x) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// Position of entry o of a list in the tiled scan layout (fb = end of the
+// list's full 128-entry blocks): transposed inside full blocks, canonical in
+// the tail.
+__device__ __forceinline__ int tiled_offset(int o, int fb) {
+    return o < fb ? ((o & ~(SC_BLK - 1)) | ((o & 31) << 2) | ((o >> 5) & 3)) : o;
+}
+
+constexpr int CH = 2 * SC_BLK;  // postings per fast item: two blocks of the tiled layout
 
 template <int PREC>
 __device__ __forceinline__ float decode_u(unsigned b) {
@@ -249,6 +311,12 @@ __device__ __forceinline__ void load_one(const AssignParams &P, int pos, int &id
 #ifndef SIVF_ASSIGN_MIN_CTAS_128
 #define SIVF_ASSIGN_MIN_CTAS_128 10
 #endif
+// resident CTAs asked of the compiler for a block size (an SM holds at most 32)
+template <int T>
+constexpr int assign_min_blocks() {
+    constexpr int b = SIVF_ASSIGN_MIN_CTAS_128 * 128 / T;
+    return b < 1 ? 1 : (b > 32 ? 32 : b);
+}
 
 // Score-vector reads and resets. A global score vector is updated by L2
 // atomics, so its plain reads and stores must not go through L1 (which is not
@@ -268,19 +336,20 @@ __device__ __forceinline__ void rho_zero(uint32_t *p) {
 // atomics) instead of shared memory; slower per posting, but independent of
 // the shared-memory size, so it serves any k and lets more CTAs reside.
 template <int T, int PREC, bool CID16, bool GRHO>
-__global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) : 1)
-    assign_kernel(AssignParams P) {
+__global__ void __launch_bounds__(T, assign_min_blocks<T>()) assign_kernel(AssignParams P) {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int NW = T / 32;
     const int kpad = (P.kmax + 3) & ~3;
     uint32_t *rho = GRHO ? P.grho + (size_t)blockIdx.x * kpad : smem;
-    float *s_vs = reinterpret_cast<float *>(GRHO ? smem : smem + kpad);
-    int *s_start = reinterpret_cast<int *>(s_vs + T);
-    int *s_len = s_start + T;
-    int *s_fb = s_len + T;
-    int *s_item = s_fb + T;
-    __shared__ int warp_i[32];
-    __shared__ int s_total;
+    // staged segment of thread h: {scan start, full-block end, end of the full
+    // fully scanned blocks, scaled value bits}, scanned length, item and
+    // row-posting prefixes
+    int4 *s_seg = reinterpret_cast<int4 *>(GRHO ? smem : smem + kpad);
+    int *s_len = reinterpret_cast<int *>(s_seg + T);
+    int *s_item = s_len + T;
+    int *s_rend = s_item + T;
+    __shared__ int2 warp_i2[32];
+    __shared__ int2 s_total2;
     __shared__ long long s_obj;
     __shared__ Top2 warp_t[NW];
     __shared__ double warp_d[NW];
@@ -325,80 +394,137 @@ __global__ void __launch_bounds__(T, (SIVF_ASSIGN_MIN_CTAS_128 * 128 / T) > 0 ? 
         const int32_t *movs = P.mov_list + mb;
 
         // ---- similarity scan (Algorithm 4, lines 7-13) ----
-        // Work items are chunks of CH = 2 blocks of 128 postings of one list
-        // (segment), starting at the segment start; only a segment's last chunk
-        // can be partial. Warp w takes a contiguous block of the items, so the
-        // owning term (and its start, lengths and value) changes rarely and
-        // stays in registers. In a full block of the tiled layout lane l reads
-        // postings l, 32+l, 64+l, 96+l with one vector load per array; step m
-        // of the warp then touches postings 32m .. 32m+31, whose ids are
-        // distinct banks on dense lists. The ragged tail (< 128 postings of a
-        // list) is read one posting per lane and step.
+        // The object's terms are staged T at a time. Each segment (the part of
+        // a term's posting list that is scanned: the front, or the whole list)
+        // splits into its full 128-entry blocks of the tiled layout whose
+        // postings are all scanned, and a remainder of fewer than 128
+        // postings (the part of a block that a front ends inside, or the
+        // list's ragged tail). Work is done in two forms:
+        //  - items: two full blocks (the last one of a segment may hold one),
+        //    or a remainder of at least RMIN postings. In a full block lane l
+        //    reads postings l, 32+l, 64+l, 96+l with one vector load per
+        //    array; step m of the warp then touches postings 32m .. 32m+31,
+        //    whose ids are distinct banks on dense lists. Warp w takes a
+        //    contiguous range of the items;
+        //  - rows: the shorter remainders of all staged segments are laid end
+        //    to end and cut into rows of 32 postings, one posting per lane, so
+        //    short fronts keep every lane busy. Warp w takes a contiguous range
+        //    of rows; each lane walks forward through the segments.
+        constexpr int RMIN = 64;
         for (int64_t cb = rb; cb < re; cb += T) {
             const int cn = (int)min((int64_t)T, re - cb);
-            int nch = 0;
+            int2 cnt = make_int2(0, 0);
             if (tid < cn) {
                 const int t = P.idx[cb + tid];
                 const int64_t o0 = P.if_off[t];
                 const int lfull = (int)(P.if_off[t + 1] - o0);
                 const int len = filt ? P.if_mf0[t] : lfull;
-                s_start[tid] = (int)P.sc_off[t];
+                const int fb = lfull & ~(SC_BLK - 1);
+                const int r0 = min(len, fb) & ~(SC_BLK - 1);  // postings in full, fully scanned blocks
+                const float vs = P.val[cb + tid] * FIX_SCALE;  // exact: power-of-two scaling
+                s_seg[tid] = make_int4((int)P.sc_off[t], fb, r0, __float_as_int(vs));
                 s_len[tid] = len;
-                s_fb[tid] = lfull & ~(SC_BLK - 1);
-                s_vs[tid] = P.val[cb + tid] * FIX_SCALE;  // exact: power-of-two scaling
-                nch = (len + CH - 1) / CH;
+                const int rem = len - r0;
+                cnt = rem >= RMIN ? make_int2((r0 + CH - 1) / CH + 1, 0) : make_int2((r0 + CH - 1) / CH, rem);
                 c_post_obj += (unsigned long long)len;
             }
-            const int incl = block_inclusive_scan_int<T>(nch, warp_i, &s_total);
-            s_item[tid] = incl;
+            const int2 incl = block_inclusive_scan_int2<T>(cnt, warp_i2, &s_total2);
+            s_item[tid] = incl.x;
+            s_rend[tid] = incl.y;
             __syncthreads();
-            const int items = s_total;
-            const int per_warp = (items + NW - 1) / NW;
-            const int it0 = warp * per_warp;
-            const int it1 = min(items, it0 + per_warp);
-            int h = 0, h_first = 0, h_end = 0, sb = 0, len = 0, fb = 0;
-            float vs = 0.f;
-            for (int it = it0; it < it1; ++it) {
-                if (it >= h_end) {
-                    while (s_item[h] <= it) ++h;
-                    h_first = h ? s_item[h - 1] : 0;
-                    h_end = s_item[h];
-                    sb = s_start[h];
-                    len = s_len[h];
-                    fb = s_fb[h];
-                    vs = s_vs[h];
+            const int2 tot = s_total2;
+
+            // items
+            {
+                const int per_warp = (tot.x + NW - 1) / NW;
+                const int it0 = warp * per_warp;
+                const int it1 = min(tot.x, it0 + per_warp);
+                if (it0 < it1) {
+                    int h = first_greater<T>(s_item, it0);
+                    int h_first = h ? s_item[h - 1] : 0, h_end = s_item[h];
+                    int4 sg = s_seg[h];
+                    for (int it = it0; it < it1; ++it) {
+                        if (it >= h_end) {
+                            do {
+                                ++h;
+                            } while (s_item[h] <= it);
+                            h_first = s_item[h - 1];
+                            h_end = s_item[h];
+                            sg = s_seg[h];
+                        }
+                        const int sb = sg.x, fb = sg.y, r0 = sg.z;
+                        const float vs = __int_as_float(sg.w);
+                        const int off = (it - h_first) * CH;
+                        if (off + SC_BLK < r0) {  // two full blocks
+                            const int pos = sb + off + 4 * lane;
+                            const Post4 a = load_tiled<PREC, CID16>(P, pos);
+                            const Post4 b = load_tiled<PREC, CID16>(P, pos + SC_BLK);
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) atomicAdd(&rho[a.id[m]], __float2uint_ru(vs * a.u[m]));
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) atomicAdd(&rho[b.id[m]], __float2uint_ru(vs * b.u[m]));
+                        } else if (off < r0) {  // the segment's odd last full block
+                            const Post4 a = load_tiled<PREC, CID16>(P, sb + off + 4 * lane);
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) atomicAdd(&rho[a.id[m]], __float2uint_ru(vs * a.u[m]));
+                        } else {  // a remainder of RMIN .. 127 postings, starting at r0
+                            const int rem = s_len[h] - r0;
+                            if (r0 < fb) {
+                                // inside a full block of the list (the load stays in it)
+                                const Post4 a = load_tiled<PREC, CID16>(P, sb + r0 + 4 * lane);
+#pragma unroll
+                                for (int m = 0; m < 4; ++m)
+                                    if (32 * m + lane < rem) atomicAdd(&rho[a.id[m]], __float2uint_ru(vs * a.u[m]));
+                            } else {  // the ragged tail, canonical order
+                                int id[4];
+                                float u[4];
+#pragma unroll
+                                for (int m = 0; m < 4; ++m)
+                                    if (32 * m + lane < rem) load_one<PREC, CID16>(P, sb + r0 + 32 * m + lane, id[m], u[m]);
+#pragma unroll
+                                for (int m = 0; m < 4; ++m)
+                                    if (32 * m + lane < rem) atomicAdd(&rho[id[m]], __float2uint_ru(vs * u[m]));
+                            }
+                        }
+                    }
                 }
-                const int off = (it - h_first) * CH;  // chunk offset inside the segment
-                if (off + CH <= len && off + CH <= fb) {
-                    // two full blocks, every posting scanned
-                    const Post4 a = load_tiled<PREC, CID16>(P, sb + off + 4 * lane);
-                    const Post4 b = load_tiled<PREC, CID16>(P, sb + off + SC_BLK + 4 * lane);
+            }
+
+            // rows: remainders shorter than RMIN, one posting per lane
+            if (tot.y > 0) {
+                constexpr int RU = 2;  // rows per step
+                const int rows = (tot.y + 31) >> 5;
+                const int per_warp = (rows + NW - 1) / NW;
+                const int w0 = warp * per_warp;
+                const int w1 = min(rows, w0 + per_warp);
+                if (w0 < w1) {
+                    int h = first_greater<T>(s_rend, min(w0 * 32 + lane, tot.y - 1));
+                    int hb = h ? s_rend[h - 1] : 0, he = s_rend[h];
+                    int4 sg = s_seg[h];
+                    for (int row = w0; row < w1; row += RU) {
+                        int id[RU];
+                        float u[RU], vv[RU];
+                        bool ok[RU];
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) atomicAdd(&rho[a.id[m]], __float2uint_ru(vs * a.u[m]));
+                        for (int m = 0; m < RU; ++m) {
+                            const int q = (row + m) * 32 + lane;
+                            ok[m] = row + m < w1 && q < tot.y;
+                            if (ok[m]) {
+                                if (q >= he) {
+                                    do {
+                                        ++h;
+                                        hb = he;
+                                        he = s_rend[h];
+                                    } while (q >= he);
+                                    sg = s_seg[h];
+                                }
+                                load_one<PREC, CID16>(P, sg.x + tiled_offset(sg.z + (q - hb), sg.y), id[m], u[m]);
+                                vv[m] = __int_as_float(sg.w);
+                            }
+                        }
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) atomicAdd(&rho[b.id[m]], __float2uint_ru(vs * b.u[m]));
-                    continue;
-                }
-#pragma unroll
-                for (int bi = 0; bi < 2; ++bi) {
-                    const int bo = off + bi * SC_BLK;
-                    if (bo >= len) break;
-                    if (bo < fb) {
-                        // a full block of the list (the loads stay inside it),
-                        // of which the front part may end inside
-                        const Post4 a = load_tiled<PREC, CID16>(P, sb + bo + 4 * lane);
-#pragma unroll
-                        for (int m = 0; m < 4; ++m)
-                            if (bo + 32 * m + lane < len) atomicAdd(&rho[a.id[m]], __float2uint_ru(vs * a.u[m]));
-                    } else {
-                        int id[4];
-                        float u[4];
-#pragma unroll
-                        for (int m = 0; m < 4; ++m)
-                            if (bo + 32 * m + lane < len) load_one<PREC, CID16>(P, sb + bo + 32 * m + lane, id[m], u[m]);
-#pragma unroll
-                        for (int m = 0; m < 4; ++m)
-                            if (bo + 32 * m + lane < len) atomicAdd(&rho[id[m]], __float2uint_ru(vs * u[m]));
+                        for (int m = 0; m < RU; ++m)
+                            if (ok[m]) atomicAdd(&rho[id[m]], __float2uint_ru(vv[m] * u[m]));
                     }
                 }
             }
@@ -604,6 +730,7 @@ template <int PREC, bool CID16, bool GRHO>
 cudaError_t launch_prec(sivf_ctx *c, const AssignParams &P) {
     const int cps = c->assign_ctas_per_sm;
     switch (c->assign_threads) {
+        case 32: return launch_t<32, PREC, CID16, GRHO>(c, P, cps);
         case 64: return launch_t<64, PREC, CID16, GRHO>(c, P, cps);
         case 128: return launch_t<128, PREC, CID16, GRHO>(c, P, cps);
         case 256: return launch_t<256, PREC, CID16, GRHO>(c, P, cps);
@@ -672,12 +799,40 @@ cudaError_t launch_assign(sivf_ctx *c) {
     }
 }
 
-// Autotuner of the assignment kernel: times every feasible (threads per CTA,
-// score buffer in shared or global memory) configuration on the live state
-// and keeps the fastest. The kernel writes labels, own scores, moving flags
-// and counters; those are restored (or reset) around each trial, so the step
-// that follows sees the state it would have seen without tuning.
+// Autotuner of the assignment kernel: times the feasible (threads per CTA,
+// score buffer in shared or global memory) configurations on the live state
+// and keeps the fastest. Every configuration is timed once, the two fastest
+// (and the default) once more. The kernel writes labels, own scores, moving
+// flags and counters; those are restored (or reset) around each trial, so the
+// step that follows sees the state it would have seen without tuning. The
+// choice is remembered for the process, keyed by device and problem shape, so
+// a later context of the same shape skips the trials.
+namespace {
+struct TuneKey {
+    int device, prec, icp;
+    int64_t N, nnz, k, kmax, n_inst;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(device, prec, icp, N, nnz, k, kmax, n_inst) <
+               std::tie(o.device, o.prec, o.icp, o.N, o.nnz, o.k, o.kmax, o.n_inst);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+}  // namespace
+
 cudaError_t autotune_assign(sivf_ctx *c) {
+    const TuneKey key{c->device, (int)c->cfg.prec, c->cfg.icp, c->N, c->nnz, c->k, c->kmax, c->n_inst};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end() && (!it->second.second || c->grho)) {
+            c->assign_threads = it->second.first;
+            c->assign_global = it->second.second;
+            c->assign_grid = 0;
+            c->tuned = true;
+            return cudaSuccess;
+        }
+    }
     cudaStream_t s = c->stream;
     Workspace &ws = c->ws;
     ws.reset();
@@ -692,45 +847,63 @@ cudaError_t autotune_assign(sivf_ctx *c) {
     int dev_smem = 0;
     SIVF_CUDA_TRY(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     const int kpad = (c->kmax + 3) & ~3;
-    const int threads[4] = {64, 128, 256, 512};
     const int def_t = c->assign_threads, def_g = c->assign_global;
-    float best = 1e30f, def_ms = 1e30f;
-    int best_t = def_t, best_g = def_g;
     cudaEvent_t e0 = c->ev[0], e1 = c->ev[1];
+    // one timed trial of configuration (t, g); 1e30 if it cannot launch here
+    auto trial = [&](int t, int g, float *ms_out) -> cudaError_t {
+        *ms_out = 1e30f;
+        SIVF_CUDA_TRY(cudaMemcpyAsync(c->own, own_snap, sizeof(uint32_t) * c->N, cudaMemcpyDeviceToDevice, s));
+        SIVF_CUDA_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
+        SIVF_CUDA_TRY(cudaMemsetAsync(c->moving, 0, c->k, s));
+        SIVF_CUDA_TRY(cudaMemsetAsync(c->inst_changed, 0, sizeof(unsigned long long) * c->n_inst, s));
+        if (g) SIVF_CUDA_TRY(cudaMemsetAsync(c->grho, 0, sizeof(uint32_t) * (size_t)c->grho_ctas * kpad, s));
+        c->assign_threads = t;
+        c->assign_global = g;
+        c->assign_grid = 0;
+        SIVF_CUDA_TRY(cudaEventRecord(e0, s));
+        cudaError_t e = launch_assign(c);
+        SIVF_CUDA_TRY(cudaEventRecord(e1, s));
+        SIVF_CUDA_TRY(cudaStreamSynchronize(s));
+        if (e != cudaSuccess) {  // configuration not launchable here: skip it
+            cudaGetLastError();
+            return cudaSuccess;
+        }
+        return cudaEventElapsedTime(ms_out, e0, e1);
+    };
+    struct Cand {
+        int t, g;
+        float ms;
+    };
+    std::vector<Cand> cands;
+    const int threads[5] = {32, 64, 128, 256, 512};
     for (int g = 0; g < 2; ++g) {
         if (g == 1 && !c->grho) continue;
         for (int t : threads) {
             if (!g && (size_t)kpad * 4 + (size_t)t * ASSIGN_STAGE_BYTES > (size_t)dev_smem) continue;
-            float trial = 1e30f;
-            for (int rep = 0; rep < 2; ++rep) {  // best of two launches
-            SIVF_CUDA_TRY(cudaMemcpyAsync(c->own, own_snap, sizeof(uint32_t) * c->N, cudaMemcpyDeviceToDevice, s));
-            SIVF_CUDA_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
-            SIVF_CUDA_TRY(cudaMemsetAsync(c->moving, 0, c->k, s));
-            SIVF_CUDA_TRY(cudaMemsetAsync(c->inst_changed, 0, sizeof(unsigned long long) * c->n_inst, s));
-            if (g) SIVF_CUDA_TRY(cudaMemsetAsync(c->grho, 0, sizeof(uint32_t) * (size_t)c->grho_ctas * kpad, s));
-            c->assign_threads = t;
-            c->assign_global = g;
-            c->assign_grid = 0;
-            SIVF_CUDA_TRY(cudaEventRecord(e0, s));
-            cudaError_t e = launch_assign(c);
-            SIVF_CUDA_TRY(cudaEventRecord(e1, s));
-            SIVF_CUDA_TRY(cudaStreamSynchronize(s));
-            if (e != cudaSuccess) {  // configuration not launchable here: skip it
-                cudaGetLastError();
-                break;
-            }
             float ms = 0.f;
-            SIVF_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            trial = ms < trial ? ms : trial;
-            }
-            if (t == def_t && g == def_g) def_ms = trial;
-            if (trial < best) {
-                best = trial;
-                best_t = t;
-                best_g = g;
-            }
+            SIVF_CUDA_TRY(trial(t, g, &ms));
+            if (ms < 1e29f) cands.push_back({t, g, ms});
         }
     }
+    std::sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b) { return a.ms < b.ms; });
+    float def_ms = 1e30f;
+    for (size_t q = 0; q < cands.size(); ++q) {
+        const bool is_def = cands[q].t == def_t && cands[q].g == def_g;
+        if (q < 2 || is_def) {  // second timing: keep the better of the two
+            float ms = 0.f;
+            SIVF_CUDA_TRY(trial(cands[q].t, cands[q].g, &ms));
+            cands[q].ms = std::min(cands[q].ms, ms);
+        }
+        if (is_def) def_ms = cands[q].ms;
+    }
+    int best_t = def_t, best_g = def_g;
+    float best = 1e30f;
+    for (const Cand &cd : cands)
+        if (cd.ms < best) {
+            best = cd.ms;
+            best_t = cd.t;
+            best_g = cd.g;
+        }
     // keep the default unless the winner is clearly faster (timing noise)
     if (def_ms < 1e29f && best > 0.97f * def_ms) {
         best_t = def_t;
@@ -745,6 +918,10 @@ cudaError_t autotune_assign(sivf_ctx *c) {
     if (best_g) SIVF_CUDA_TRY(cudaMemsetAsync(c->grho, 0, sizeof(uint32_t) * (size_t)c->grho_ctas * kpad, s));
     SIVF_CUDA_TRY(cudaStreamSynchronize(s));
     ws.reset();
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = {best_t, best_g};
+    }
     return cudaSuccess;
 }
 

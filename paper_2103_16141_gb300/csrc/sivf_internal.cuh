@@ -42,8 +42,9 @@ constexpr int64_t IF_PAD = 256;
 // block of the tiled scan layout: 32 lanes x 4 entries
 constexpr int SC_BLK = 128;
 // shared memory the assignment kernel stages per thread besides the score
-// vector: list start, scanned length, full-block end, scaled value, item prefix
-constexpr int ASSIGN_STAGE_BYTES = 20;
+// vector: list start, full-block end, end of the full scanned blocks, scaled
+// value, scanned length, item prefix, row-posting prefix
+constexpr int ASSIGN_STAGE_BYTES = 28;
 // Scores are accumulated as unsigned fixed point with quantum 2^-31:
 // q = ceil(fl(v * u) * 2^31). Cosine scores are <= 1 (+ rounding), so the
 // sum of an object's terms stays below 2^32.

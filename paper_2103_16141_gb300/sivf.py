@@ -22,7 +22,7 @@ SCORE_BUFFERS = {"auto": 0, "shared": 1, "global": 2}
 class sivf_config(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("icp", ctypes.c_int), ("threads", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("mem_cap_bytes", ctypes.c_int64), ("use_graph", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("score_buffer", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("score_buffer", ctypes.c_int), ("inputs_on_host", ctypes.c_int)]
 
 
 class sivf_stats(ctypes.Structure):
@@ -194,11 +194,15 @@ class SIVF:
     device, or numpy arrays that are copied to the device. The object keeps
     references to the device tensors for as long as the context lives, as the
     library borrows them.
+
+    inputs_on_host=True passes HOST arrays (numpy, or CPU tensors, pinned for
+    an asynchronous copy) straight to sivf_init, which copies them into device
+    buffers of its own.
     """
 
     def __init__(self, row_ptr, idx, val, D: int, k: int, init_ids, precision: str = "fp32", icp: bool = True,
                  threads: int = 0, ctas_per_sm: int = 0, mem_cap_bytes: int = 0, stream=None, use_graph: bool = False,
-                 autotune: bool = False, score_buffer: str = "auto"):
+                 autotune: bool = False, score_buffer: str = "auto", inputs_on_host: bool = False):
         import numpy as np
         import torch
 
@@ -209,17 +213,34 @@ class SIVF:
                 return a.to(device=dev, dtype=dtype).contiguous()
             return torch.from_numpy(np.ascontiguousarray(a)).to(device=dev, dtype=dtype)
 
-        self.row_ptr = to_dev(row_ptr, torch.int64)
-        self.idx = to_dev(idx, torch.int32)
-        self.val = to_dev(val, torch.float32)
-        self.N = int(self.row_ptr.numel() - 1)
+        def host(a, dtype):
+            if isinstance(a, torch.Tensor):
+                if a.is_cuda or a.dtype != dtype or not a.is_contiguous():
+                    raise ValueError("inputs_on_host expects contiguous CPU tensors of the CSR dtypes")
+                return a, a.data_ptr()
+            a = np.ascontiguousarray(a, dtype={torch.int64: np.int64, torch.int32: np.int32,
+                                               torch.float32: np.float32}[dtype])
+            return a, a.ctypes.data
+
+        if inputs_on_host:
+            # nothing is borrowed: the library copies the host arrays at init
+            (rp, rp_p), (ix, ix_p), (vl, vl_p) = (host(row_ptr, torch.int64), host(idx, torch.int32),
+                                                  host(val, torch.float32))
+            self.row_ptr = self.idx = self.val = None
+            self.N = int(len(rp) - 1)
+        else:
+            self.row_ptr = to_dev(row_ptr, torch.int64)
+            self.idx = to_dev(idx, torch.int32)
+            self.val = to_dev(val, torch.float32)
+            rp_p, ix_p, vl_p = self.row_ptr.data_ptr(), self.idx.data_ptr(), self.val.data_ptr()
+            self.N = int(self.row_ptr.numel() - 1)
         self.D, self.k = int(D), int(k)
         ini = np.ascontiguousarray(np.asarray(init_ids, dtype=np.int32))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         cfg = sivf_config(PRECISIONS[precision], int(bool(icp)), int(threads), int(ctas_per_sm), int(mem_cap_bytes),
-                          int(bool(use_graph)), int(bool(autotune)), SCORE_BUFFERS[score_buffer])
-        self.ctx = sivf_init(cfg, self.N, self.D, self.k, self.row_ptr.data_ptr(), self.idx.data_ptr(),
-                             self.val.data_ptr(), ini.ctypes.data, self.stream.cuda_stream)
+                          int(bool(use_graph)), int(bool(autotune)), SCORE_BUFFERS[score_buffer],
+                          int(bool(inputs_on_host)))
+        self.ctx = sivf_init(cfg, self.N, self.D, self.k, rp_p, ix_p, vl_p, ini.ctypes.data, self.stream.cuda_stream)
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -248,9 +269,6 @@ class SIVF:
 
     def stats(self) -> dict:
         return sivf_get_stats(self.ctx).as_dict()
-
-    def last_error(self) -> str:
-        return (load().sivf_last_error(self.ctx) or b"").decode(errors="replace")
 
     def last_error(self) -> str:
         return (load().sivf_last_error(self.ctx) or b"").decode(errors="replace")

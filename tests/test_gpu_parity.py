@@ -27,7 +27,7 @@ def test_c1_lockstep_fp32_icp():
     assert recs[-1]["changed"] == 0 or len(recs) == w.max_iter
 
 
-@pytest.mark.parametrize("threads", [64, 128, 512])
+@pytest.mark.parametrize("threads", [32, 64, 128, 512])
 def test_mid_lockstep_block_sizes(threads):
     # several tiles of objects, documents longer than one staging chunk, ragged tails
     w = CONFIGS["c2"].scaled(N=6_000, D=8_000, k=60, hi=1500)
@@ -292,6 +292,29 @@ def test_autotuned_run_equals_default_run():
         assert np.array_equal(a.labels(), b.labels())
         st = b.stats()
         assert st["assign_threads"] in (64, 128, 256, 512)
+    finally:
+        a.close()
+        b.close()
+
+
+def test_host_inputs_equal_device_inputs():
+    """inputs_on_host: the library copies a pinned host CSR itself; the run is
+    the same as from borrowed device arrays, and the host arrays may be
+    released right after init."""
+    import torch
+    w = CONFIGS["c2"].scaled(N=6_000, D=8_000, k=90)
+    c, ini = corpus_for(w, seed=37)
+    a = gpu_instance(c, w.k, ini)
+    rp = torch.from_numpy(c.row_ptr.copy()).pin_memory()
+    ix = torch.from_numpy(c.idx.copy()).pin_memory()
+    vl = torch.from_numpy(c.val.copy()).pin_memory()
+    from paper_2103_16141_gb300 import SIVF
+    b = SIVF(rp, ix, vl, c.D, w.k, ini, inputs_on_host=True)
+    del rp, ix, vl
+    try:
+        ra, rb = a.run(40), b.run(40)
+        assert ra == rb
+        assert np.array_equal(a.labels(), b.labels())
     finally:
         a.close()
         b.close()
