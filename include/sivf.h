@@ -69,6 +69,15 @@ typedef struct {
                             is remembered for the process (per device and problem
                             shape), so later contexts of the same shape skip the trials */
     int score_buffer;    /* 0: automatic (shared memory when k fits), 1: shared, 2: global */
+    int update_mode;     /* cluster sums of the update step: 0 automatic (dense when the
+                            accumulator takes at most half of the free device memory
+                            and fits mem_cap_bytes), 1 dense, 2 sort. Dense: one int64
+                            fixed-point accumulator row of D entries per cluster
+                            (8 k D bytes; per instance for batches), filled with
+                            integer atomics and compacted in ascending term order.
+                            Sort: the members' (cluster, term, value) tuples are
+                            radix-sorted and equal (cluster, term) runs summed in
+                            FP64 in member order. Both are deterministic. */
     int inputs_on_host;  /* sivf_init only. 1: row_ptr / idx / val are HOST memory; the
                             library copies them (on the stream, asynchronously when the host
                             memory is pinned) into device buffers it owns and frees in
@@ -98,6 +107,7 @@ typedef struct {
     int64_t graph_iters;     /* iterations the last sivf_run / sivf_batch_run ran inside its CUDA graph */
     int32_t assign_threads;  /* threads per CTA of the assignment kernel in use */
     int32_t assign_global;   /* 1 if its score vectors live in global memory */
+    int32_t update_dense;    /* 1 if the update step sums into the dense accumulator */
 } sivf_stats;
 
 typedef struct sivf_ctx sivf_ctx; /* opaque, library-owned */

@@ -52,7 +52,7 @@ void free_all(sivf_ctx *c) {
                     c->cval[0], c->cval[1], c->cclu, c->if_off, c->if_mf0, c->if_cid, c->if_val, c->sc_off, c->sc_id16, c->sc_id32, c->sc_val, c->sc_pack, c->sc_lp,
                     c->ctr, c->obj_dev, c->ws.base, c->inst_obj, c->inst_k, c->mov_beg, c->clu_koff,
                     c->inst_changed, c->own_row_ptr, c->own_idx, c->own_val, c->clu_doff,
-                    c->loop_dev, c->done_dev, c->objf_dev, c->grho};
+                    c->loop_dev, c->done_dev, c->objf_dev, c->grho, c->acc, c->acc_off};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     destroy_loop_graph(c);
@@ -232,12 +232,43 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
     INIT_CUDA(dmalloc(c, &c->done_dev, ni), "alloc");
     INIT_CUDA(dmalloc(c, &c->objf_dev, ni), "alloc");
     {
+        // dense update accumulator: one row of the instance's D terms per cluster
+        std::vector<int64_t> aoff((size_t)k + 1, 0);
+        int64_t nmax = 1;
+        for (int32_t m = 0; m < ni; ++m) {
+            nmax = std::max(nmax, inst_obj[(size_t)m + 1] - inst_obj[(size_t)m]);
+            for (int32_t j = inst_k[(size_t)m]; j < inst_k[(size_t)m + 1]; ++j)
+                aoff[(size_t)j + 1] = aoff[(size_t)j] + (inst_d[(size_t)m + 1] - inst_d[(size_t)m]);
+        }
+        const size_t acc_bytes = 8 * (size_t)aoff[(size_t)k];
+        bool dense = c->cfg.update_mode == 1;
+        if (c->cfg.update_mode == 0) {
+            size_t free_b = 0, total_b = 0;
+            INIT_CUDA(cudaMemGetInfo(&free_b, &total_b), "mem info");
+            dense = acc_bytes <= free_b / 2 &&
+                    (c->cfg.mem_cap_bytes <= 0 || c->owned_bytes + acc_bytes <= (size_t)c->cfg.mem_cap_bytes);
+        }
+        if (dense) {
+            INIT_CUDA(dmalloc(c, &c->acc, (size_t)aoff[(size_t)k]), "alloc accumulator");
+            INIT_CUDA(dmalloc(c, &c->acc_off, (size_t)k + 1), "alloc");
+            INIT_CUDA(cudaMemsetAsync(c->acc, 0, acc_bytes, c->stream), "memset");
+            INIT_CUDA(cudaMemcpyAsync(c->acc_off, aoff.data(), sizeof(int64_t) * ((size_t)k + 1),
+                                      cudaMemcpyHostToDevice, c->stream), "copy");
+            INIT_CUDA(cudaStreamSynchronize(c->stream), "sync");
+            // a cluster holds at most nmax objects of values <= 1, each rounded
+            // up by less than one unit: sums stay below 2^62 + nmax
+            c->acc_shift = 62 - bits_for((uint64_t)nmax);
+            c->dense = true;
+        }
+    }
+    {
         // workspace: max of the update's two phases, plus primitive scratch
         const size_t n8 = (size_t)N * 8, k8 = (size_t)k * 8;
         // u1: 4 label key/value arrays (4 B x N), tuple counts/offsets (8 B x N),
-        // per-cluster arrays; u2 per tuple: 4 sort arrays, term, rank, value,
-        // sorted value, 64-bit key, piece sum, unique term and sum (60 B)
-        size_t phase1 = 4 * (size_t)N * 4 + 2 * n8 + 14 * k8 + 64 * ((size_t)nnz + 1) + 32 * 4096;
+        // per-cluster arrays; u2 per tuple (sort mode only): 4 sort arrays,
+        // term, rank, value, sorted value, 64-bit key, piece sum, unique term
+        // and sum (60 B)
+        size_t phase1 = 4 * (size_t)N * 4 + 2 * n8 + 14 * k8 + (c->dense ? 0 : 64 * ((size_t)nnz + 1)) + 32 * 4096;
         size_t phase2 = 16 * ((size_t)capc + 1) + 32 * ((size_t)D + 1) + 16 * 4096;
         size_t ws = phase1 > phase2 ? phase1 : phase2;
         size_t maxn = (size_t)(capc > N ? capc : N);
@@ -796,6 +827,7 @@ sivf_status sivf_get_stats(sivf_ctx *c, sivf_stats *out) {
     c->stats.launches = (int64_t)(g_launches - c->launch_base);
     c->stats.assign_threads = c->assign_threads;
     c->stats.assign_global = c->assign_global;
+    c->stats.update_dense = c->dense ? 1 : 0;
     *out = c->stats;
     return SIVF_OK;
 }

@@ -140,6 +140,14 @@ struct sivf_ctx {
     uint16_t *sc_lp = nullptr;    // 32-bit ids and 16-bit values
     int64_t cap_s = 0;            // entries of each scan array
 
+    // dense update accumulator: cluster j owns acc[acc_off[j] .. acc_off[j+1]),
+    // one int64 per term of its instance, in units of 2^-acc_shift; all zero
+    // between update steps
+    bool dense = false;
+    int64_t *acc = nullptr;
+    int64_t *acc_off = nullptr;
+    int acc_shift = 0;
+
     // counters and step scratch
     sivf::DevCounters *ctr = nullptr;
     sivf::DevCounters *ctr_host = nullptr;  // pinned mirror

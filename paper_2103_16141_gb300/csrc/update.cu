@@ -433,6 +433,173 @@ __global__ void __launch_bounds__(1024) k_sum_inst(const int32_t *inst_k, const 
     }
 }
 
+// ---------------- u2-u4, dense accumulator form ----------------
+//
+// Cluster sums in fixed point: every member value x of a recomputed cluster
+// adds ceil(x * 2^shift) to the cluster's accumulator entry of its term with
+// an integer atomic. Integer sums do not depend on the order of the adds, so
+// the result is deterministic; it exceeds the exact sum by less than one unit
+// 2^-shift per member. The rows are then read in ascending term order.
+
+__global__ void k_label_counts(int64_t N, const int32_t *labels, int64_t *cnt) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(reinterpret_cast<unsigned long long *>(cnt + labels[i]), 1ull);
+}
+
+// One warp per object of a recomputed cluster: its values into the cluster's row.
+__global__ void k_acc_scatter(int64_t N, const int32_t *labels, const int64_t *flag, const int64_t *row_ptr,
+                              const int32_t *idx, const float *val, const int32_t *clu_doff, const int64_t *acc_off,
+                              float fscale, int64_t *acc, int64_t *moved) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    long long mv = 0;
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < N; i += nw) {
+        const int32_t j = labels[i];
+        if (!flag[j]) continue;
+        const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
+        unsigned long long *row = reinterpret_cast<unsigned long long *>(acc + acc_off[j] - clu_doff[j]);
+        for (int64_t h = rb + lane; h < re; h += 32)
+            atomicAdd(row + idx[h], (unsigned long long)__float2ll_ru(val[h] * fscale));
+        mv += re - rb;
+    }
+    if (lane == 0 && mv) atomicAdd(reinterpret_cast<unsigned long long *>(moved), (unsigned long long)mv);
+}
+
+__device__ __forceinline__ long long block_sum_ll(long long x, long long *sh) {
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int s = WR_THREADS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    const long long r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Pass 1, one CTA per cluster: size of the new row, ||s_j|| in FP64 (strided
+// per-thread sums, fixed tree) and <s_j, mu_j^[r-1]> over the previous row.
+// Other clusters keep their row (sizes and objective pieces as in k_write_rows).
+__global__ void __launch_bounds__(WR_THREADS) k_acc_rows1(
+    int32_t k, const int64_t *flag, const int64_t *cnt, const int64_t *acc_off, const int32_t *clu_doff,
+    const int64_t *acc, double inv_scale, const int64_t *coff_old, const int32_t *cterm_old, const float *cval_old,
+    const double *snorm_old, int64_t *sz, double *snorm_new, double *jA, double *jU) {
+    __shared__ double sh[WR_THREADS];
+    __shared__ long long shl[WR_THREADS];
+    const int j = blockIdx.x;
+    if (j >= k) return;
+    const int64_t cb = coff_old[j], ce = coff_old[j + 1];
+    if (!flag[j]) {
+        if (threadIdx.x == 0) {
+            const double sn = cnt[j] > 0 ? snorm_old[j] : 0.0;
+            sz[j] = ce - cb;
+            snorm_new[j] = sn;
+            jA[j] = sn;  // unchanged members: <s_j, s_j / ||s_j||> = ||s_j||
+            jU[j] = sn;
+        }
+        return;
+    }
+    const int64_t base = acc_off[j], L = acc_off[j + 1] - base;
+    long long nz = 0;
+    double ss = 0.0;
+    for (int64_t t = threadIdx.x; t < L; t += WR_THREADS) {
+        const long long v = acc[base + t];
+        if (v) {
+            ++nz;
+            const double x = (double)v * inv_scale;
+            ss += x * x;
+        }
+    }
+    nz = block_sum_ll(nz, shl);
+    const double nrm = sqrt(block_sum_fixed(ss, sh));
+    double dot = 0.0;
+    const int32_t doff = clu_doff[j];
+    for (int64_t q = cb + threadIdx.x; q < ce; q += WR_THREADS)
+        dot += (double)acc[base + (cterm_old[q] - doff)] * inv_scale * (double)cval_old[q];
+    dot = block_sum_fixed(dot, sh);
+    if (threadIdx.x == 0) {
+        sz[j] = nz;
+        snorm_new[j] = nrm;
+        jA[j] = dot;
+        jU[j] = nrm;
+    }
+}
+
+// Pass 2, one CTA per cluster: the new row in ascending term order (block
+// compaction of the non-zero entries), u = s / ||s|| as FP32, and the
+// accumulator row cleared for the next step. Other clusters copy their row.
+__global__ void __launch_bounds__(WR_THREADS) k_acc_rows2(
+    int32_t k, const int64_t *flag, const int64_t *acc_off, const int32_t *clu_doff, int64_t *acc,
+    double inv_scale, const int64_t *coff_old, const int32_t *cterm_old, const float *cval_old,
+    const double *snorm_new, const int64_t *coff_new, int32_t *cterm_new, float *cval_new, int32_t *cclu_new,
+    int64_t cap, unsigned long long *error) {
+    constexpr int PER = 4;  // entries per thread and chunk
+    constexpr int NWR = WR_THREADS / 32;
+    __shared__ int warp_n[NWR];
+    const int j = blockIdx.x;
+    if (j >= k) return;
+    const bool over = coff_new[k] > cap;  // more entries than the buffers hold: write nothing, report
+    if (over && j == 0 && threadIdx.x == 0) atomicOr(error, 1ull);
+    const int64_t o0 = coff_new[j];
+    if (!flag[j]) {
+        if (over) return;
+        const int64_t cb = coff_old[j], ce = coff_old[j + 1];
+        for (int64_t q = cb + threadIdx.x; q < ce; q += WR_THREADS) {
+            cterm_new[o0 + (q - cb)] = cterm_old[q];
+            cval_new[o0 + (q - cb)] = cval_old[q];
+            cclu_new[o0 + (q - cb)] = j;
+        }
+        return;
+    }
+    const int64_t base = acc_off[j], L = acc_off[j + 1] - base;
+    const int32_t doff = clu_doff[j];
+    const double nrm = snorm_new[j];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t o = o0;
+    for (int64_t c0 = 0; c0 < L; c0 += (int64_t)WR_THREADS * PER) {
+        // thread tid takes entries c0 + tid*PER .. +PER-1: ascending in tid
+        long long v[PER];
+        int n = 0;
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int64_t t = c0 + (int64_t)threadIdx.x * PER + m;
+            v[m] = t < L ? acc[base + t] : 0;
+            n += v[m] != 0;
+        }
+        int inc = n;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += y;
+        }
+        if (lane == 31) warp_n[warp] = inc;
+        __syncthreads();
+        int before = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < NWR; ++w) {
+            const int x = warp_n[w];
+            before += w < warp ? x : 0;
+            total += x;
+        }
+        int64_t p = o + before + (inc - n);
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            if (v[m]) {
+                const int64_t t = c0 + (int64_t)threadIdx.x * PER + m;
+                if (!over) {
+                    cterm_new[p] = (int32_t)t + doff;
+                    cval_new[p] = (float)((double)v[m] * inv_scale / nrm);
+                    cclu_new[p] = j;
+                }
+                acc[base + t] = 0;
+                ++p;
+            }
+        }
+        o += total;
+        __syncthreads();  // warp_n is rewritten by the next chunk
+    }
+}
+
 // ---------------- u5: structured inverted file ----------------
 
 __global__ void k_if_keys(const int64_t *n_dev, int64_t cap, const int32_t *cterm, const int32_t *cclu,
@@ -618,6 +785,51 @@ cudaError_t build_inverted_file(sivf_ctx *c) {
     return cudaSuccess;
 }
 
+// Update step with the dense accumulator (u1: member counts only; u2-u4 as
+// above; u5 as in the sort form).
+cudaError_t run_update_dense(sivf_ctx *c) {
+    cudaStream_t s = c->stream;
+    Workspace &ws = c->ws;
+    ws.reset();
+    const int64_t N = c->N;
+    const int32_t k = c->k;
+    const int cur = c->cur, nw = 1 - c->cur;
+    int64_t *cnt = ws.take<int64_t>(k), *flag = ws.take<int64_t>(k);
+    int64_t *sz = ws.take<int64_t>((size_t)k + 1), *newn_d = ws.take<int64_t>(1), *moved_d = ws.take<int64_t>(1);
+    double *jAd = ws.take<double>(k), *jUd = ws.take<double>(k);
+    if (!cnt || !flag || !sz || !newn_d || !moved_d || !jAd || !jUd) return cudaErrorMemoryAllocation;
+    SIVF_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * k, s));
+    SIVF_CUDA_TRY(cudaMemsetAsync(moved_d, 0, sizeof(int64_t), s));
+    k_label_counts<<<blocks_for(N), TPB, 0, s>>>(N, c->labels, cnt);
+    k_recompute_flags<<<blocks_for(k), TPB, 0, s>>>(k, c->lam, cnt, flag);
+    const float fscale = ldexpf(1.0f, c->acc_shift);
+    const double inv_scale = ldexp(1.0, -c->acc_shift);
+    k_acc_scatter<<<blocks_for(N * 32), TPB, 0, s>>>(N, c->labels, flag, c->row_ptr, c->idx, c->val, c->clu_doff,
+                                                     c->acc_off, fscale, c->acc, moved_d);
+    k_acc_rows1<<<(unsigned)k, WR_THREADS, 0, s>>>(k, flag, cnt, c->acc_off, c->clu_doff, c->acc, inv_scale,
+                                                   c->coff[cur], c->cterm[cur], c->cval[cur], c->snorm, sz,
+                                                   c->snorm_new, jAd, jUd);
+    note_launch(4);
+    SIVF_CUDA_TRY(cudaGetLastError());
+    SIVF_CUDA_TRY(scan_exclusive_i64(sz, c->coff[nw], k, newn_d, ws, s));
+    SIVF_CUDA_TRY(cudaMemcpyAsync(c->coff[nw] + k, newn_d, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    k_acc_rows2<<<(unsigned)k, WR_THREADS, 0, s>>>(k, flag, c->acc_off, c->clu_doff, c->acc, inv_scale, c->coff[cur],
+                                                   c->cterm[cur], c->cval[cur], c->snorm_new, c->coff[nw],
+                                                   c->cterm[nw], c->cval[nw], c->cclu, c->cap_c, &c->ctr->error);
+    k_sum_inst<<<(unsigned)c->n_inst, 1024, 0, s>>>(c->inst_k, jAd, jUd, c->obj_dev);
+    k_copy_back<<<blocks_for(c->cap_c), TPB, 0, s>>>(k, c->cap_c, c->coff[nw], c->cterm[nw], c->cval[nw],
+                                                     c->snorm_new, c->coff[cur], c->cterm[cur], c->cval[cur],
+                                                     c->snorm);
+    note_launch(3);
+    SIVF_CUDA_TRY(cudaGetLastError());
+    SIVF_CUDA_TRY(cudaMemcpyAsync(&c->ctr->moved, moved_d, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    SIVF_CUDA_TRY(cudaMemcpyAsync(&c->ctr->c_nnz, newn_d, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    ws.reset();
+    SIVF_CUDA_TRY(build_inverted_file(c));
+    ws.reset();
+    return cudaSuccess;
+}
+
 // One update step (Algorithm 5). Every size that depends on the data stays on
 // the device, so the whole step can be captured in a CUDA graph.
 cudaError_t run_update(sivf_ctx *c) {
@@ -628,6 +840,8 @@ cudaError_t run_update(sivf_ctx *c) {
     const int32_t k = c->k;
     const int64_t Tmax = c->nnz > 0 ? c->nnz : 1;
     const int cur = c->cur, nw = 1 - c->cur;
+
+    if (c->dense) return run_update_dense(c);
 
     // u1: members grouped by cluster, ascending object id
     uint32_t *lk0 = ws.take<uint32_t>(N), *lv0 = ws.take<uint32_t>(N);

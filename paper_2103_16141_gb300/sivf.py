@@ -17,12 +17,14 @@ STATUS_NAMES = ["SIVF_OK", "SIVF_ERR_INVALID_ARG", "SIVF_ERR_BAD_CSR", "SIVF_ERR
                 "SIVF_ERR_TIMEOUT", "SIVF_ERR_STATE"]
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
 SCORE_BUFFERS = {"auto": 0, "shared": 1, "global": 2}
+UPDATE_MODES = {"auto": 0, "dense": 1, "sort": 2}
 
 
 class sivf_config(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("icp", ctypes.c_int), ("threads", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("mem_cap_bytes", ctypes.c_int64), ("use_graph", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("score_buffer", ctypes.c_int), ("inputs_on_host", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("score_buffer", ctypes.c_int), ("update_mode", ctypes.c_int),
+                ("inputs_on_host", ctypes.c_int)]
 
 
 class sivf_stats(ctypes.Structure):
@@ -33,7 +35,7 @@ class sivf_stats(ctypes.Structure):
                 ("objective_assign", ctypes.c_double), ("objective_update", ctypes.c_double),
                 ("ms_assign", ctypes.c_double), ("ms_update", ctypes.c_double), ("launches", ctypes.c_int64),
                 ("graph_iters", ctypes.c_int64), ("assign_threads", ctypes.c_int32),
-                ("assign_global", ctypes.c_int32)]
+                ("assign_global", ctypes.c_int32), ("update_dense", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -202,7 +204,8 @@ class SIVF:
 
     def __init__(self, row_ptr, idx, val, D: int, k: int, init_ids, precision: str = "fp32", icp: bool = True,
                  threads: int = 0, ctas_per_sm: int = 0, mem_cap_bytes: int = 0, stream=None, use_graph: bool = False,
-                 autotune: bool = False, score_buffer: str = "auto", inputs_on_host: bool = False):
+                 autotune: bool = False, score_buffer: str = "auto", inputs_on_host: bool = False,
+                 update_mode: str = "auto"):
         import numpy as np
         import torch
 
@@ -239,7 +242,7 @@ class SIVF:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         cfg = sivf_config(PRECISIONS[precision], int(bool(icp)), int(threads), int(ctas_per_sm), int(mem_cap_bytes),
                           int(bool(use_graph)), int(bool(autotune)), SCORE_BUFFERS[score_buffer],
-                          int(bool(inputs_on_host)))
+                          UPDATE_MODES[update_mode], int(bool(inputs_on_host)))
         self.ctx = sivf_init(cfg, self.N, self.D, self.k, rp_p, ix_p, vl_p, ini.ctypes.data, self.stream.cuda_stream)
 
     def close(self):
@@ -357,7 +360,8 @@ class SIVFBatch:
     """
 
     def __init__(self, corpora, ks, init_ids, precision: str = "fp32", icp: bool = True, threads: int = 0,
-                 ctas_per_sm: int = 0, use_graph: bool = False, autotune: bool = False, score_buffer: str = "auto"):
+                 ctas_per_sm: int = 0, use_graph: bool = False, autotune: bool = False, score_buffer: str = "auto",
+                 update_mode: str = "auto"):
         import numpy as np
         import torch
 
@@ -376,7 +380,8 @@ class SIVFBatch:
         self.Ns = [d.N for d in descs]
         self.ks = [int(k) for k in ks]
         cfg = sivf_config(PRECISIONS[precision], int(bool(icp)), int(threads), int(ctas_per_sm), 0,
-                          int(bool(use_graph)), int(bool(autotune)), SCORE_BUFFERS[score_buffer])
+                          int(bool(use_graph)), int(bool(autotune)), SCORE_BUFFERS[score_buffer],
+                          UPDATE_MODES[update_mode])
         self.ctx = sivf_batch_init(cfg, descs)
         self._keep = None  # the library copied the corpora
 

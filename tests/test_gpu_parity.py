@@ -20,11 +20,22 @@ from tests.helpers import random_dense_corpus
 pytestmark = pytest.mark.gpu
 
 
-def test_c1_lockstep_fp32_icp():
+@pytest.mark.parametrize("update_mode", ["dense", "sort"])
+def test_c1_lockstep_fp32_icp(update_mode):
     w = CONFIGS["c1"]
     c, ini = corpus_for(w)
-    recs = lockstep(c, w.k, ini, w.max_iter)
+    recs = lockstep(c, w.k, ini, w.max_iter, update_mode=update_mode)
     assert recs[-1]["changed"] == 0 or len(recs) == w.max_iter
+    assert all(r["stats"]["update_dense"] == (update_mode == "dense") for r in recs)
+
+
+@pytest.mark.parametrize("update_mode", ["dense", "sort"])
+def test_update_modes_on_long_lists(update_mode):
+    """Both forms of the update step (dense fixed-point accumulator, sorted
+    FP64 runs) against the oracle's centroids and objectives."""
+    w = CONFIGS["c2"].scaled(N=8_000, D=1_500, k=500, mu=3.5, hi=400)
+    c, ini = corpus_for(w, seed=41)
+    lockstep(c, w.k, ini, 10, update_mode=update_mode)
 
 
 @pytest.mark.parametrize("threads", [32, 64, 128, 512])
@@ -166,13 +177,13 @@ def _batch_corpora(n_inst, scale, seed0=0):
     return ws, cs, inis
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16"])
-def test_batched_instances_match_their_own_oracles(precision):
+@pytest.mark.parametrize("precision,update_mode", [("fp32", "dense"), ("fp16", "dense"), ("fp32", "sort")])
+def test_batched_instances_match_their_own_oracles(precision, update_mode):
     """Several uneven instances in one context: at every iteration each
     instance's labels equal its own FP64 oracle's (near ties excepted)."""
     from paper_2103_16141_gb300 import SIVFBatch
     ws, cs, inis = _batch_corpora(6, scale=0.05)
-    b = SIVFBatch(cs, [w.k for w in ws], inis, precision=precision)
+    b = SIVFBatch(cs, [w.k for w in ws], inis, precision=precision, update_mode=update_mode)
     ors = [Oracle(c, w.k, ini, icp=True) for w, c, ini in zip(ws, cs, inis)]
     ous = [Oracle(c, w.k, ini, icp=False) for w, c, ini in zip(ws, cs, inis)]
     done = [False] * len(ws)
@@ -224,14 +235,15 @@ def test_batched_run_equals_separate_runs():
         b.close()
 
 
-def test_graph_loop_equals_host_stepped_run():
+@pytest.mark.parametrize("update_mode", ["dense", "sort"])
+def test_graph_loop_equals_host_stepped_run(update_mode):
     """With use_graph the iterations after the second run inside one CUDA graph
     (WHILE conditional node): same labels, iteration count, objective and
     centroids as the host-stepped run."""
     w = CONFIGS["c2"].scaled(N=8_000, D=10_000, k=80)
     c, ini = corpus_for(w, seed=17)
-    a = gpu_instance(c, w.k, ini, use_graph=False)
-    b = gpu_instance(c, w.k, ini, use_graph=True)
+    a = gpu_instance(c, w.k, ini, use_graph=False, update_mode=update_mode)
+    b = gpu_instance(c, w.k, ini, use_graph=True, update_mode=update_mode)
     try:
         ia, oa = a.run(40)
         ib, ob = b.run(40)
