@@ -73,8 +73,10 @@ typedef struct {
                             accumulator takes at most half of the free device memory
                             and fits mem_cap_bytes), 1 dense, 2 sort. Dense: one int64
                             fixed-point accumulator row of D entries per cluster
-                            (8 k D bytes; per instance for batches), filled with
-                            integer atomics and compacted in ascending term order.
+                            (8 k D bytes; per instance for batches), kept across
+                            steps and updated with integer atomics for the objects
+                            whose label changed, then compacted in ascending term
+                            order for the moving clusters.
                             Sort: the members' (cluster, term, value) tuples are
                             radix-sorted and equal (cluster, term) runs summed in
                             FP64 in member order. Both are deterministic. */
@@ -98,7 +100,9 @@ typedef struct {
     int64_t rescored;        /* objects re-scored in FP64 (top-2 margin inside the error bound) */
     int64_t rescore_cands;   /* candidate centroids re-scored in FP64 */
     int64_t centroid_nnz;    /* non-zeros of the centroid set M^[r] after the last update */
-    int64_t moved_nnz;       /* object non-zeros gathered by the last update (members of moving clusters) */
+    int64_t moved_nnz;       /* object non-zeros the last update read: sort form, every member
+                                of a recomputed cluster; dense form, the objects whose label
+                                changed, counted once per cluster row touched */
     double objective_assign; /* J^[r] = sum_i <x_i, mu_{a(i)}^[r-1]> (FP64) */
     double objective_update; /* sum_j ||s_j^[r]||, s_j = sum of members (FP64) */
     double ms_assign;        /* device time of the last assignment step */

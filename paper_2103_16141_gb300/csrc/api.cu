@@ -52,7 +52,7 @@ void free_all(sivf_ctx *c) {
                     c->cval[0], c->cval[1], c->cclu, c->if_off, c->if_mf0, c->if_cid, c->if_val, c->sc_off, c->sc_id16, c->sc_id32, c->sc_val, c->sc_pack, c->sc_lp,
                     c->ctr, c->obj_dev, c->ws.base, c->inst_obj, c->inst_k, c->mov_beg, c->clu_koff,
                     c->inst_changed, c->own_row_ptr, c->own_idx, c->own_val, c->clu_doff,
-                    c->loop_dev, c->done_dev, c->objf_dev, c->grho, c->acc, c->acc_off};
+                    c->loop_dev, c->done_dev, c->objf_dev, c->grho, c->acc, c->acc_off, c->acc_lab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     destroy_loop_graph(c);
@@ -251,13 +251,14 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
         if (dense) {
             INIT_CUDA(dmalloc(c, &c->acc, (size_t)aoff[(size_t)k]), "alloc accumulator");
             INIT_CUDA(dmalloc(c, &c->acc_off, (size_t)k + 1), "alloc");
-            INIT_CUDA(cudaMemsetAsync(c->acc, 0, acc_bytes, c->stream), "memset");
+            INIT_CUDA(dmalloc(c, &c->acc_lab, (size_t)N), "alloc");
             INIT_CUDA(cudaMemcpyAsync(c->acc_off, aoff.data(), sizeof(int64_t) * ((size_t)k + 1),
                                       cudaMemcpyHostToDevice, c->stream), "copy");
             INIT_CUDA(cudaStreamSynchronize(c->stream), "sync");
             // a cluster holds at most nmax objects of values <= 1, each rounded
             // up by less than one unit: sums stay below 2^62 + nmax
             c->acc_shift = 62 - bits_for((uint64_t)nmax);
+            c->acc_total = aoff[(size_t)k];
             c->dense = true;
         }
     }

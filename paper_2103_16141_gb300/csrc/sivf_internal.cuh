@@ -141,11 +141,14 @@ struct sivf_ctx {
     int64_t cap_s = 0;            // entries of each scan array
 
     // dense update accumulator: cluster j owns acc[acc_off[j] .. acc_off[j+1]),
-    // one int64 per term of its instance, in units of 2^-acc_shift; all zero
-    // between update steps
+    // one int64 per term of its instance, in units of 2^-acc_shift. It holds
+    // the fixed-point sums of the members recorded in acc_lab (the label each
+    // object was last added under, -1 = none) and is updated incrementally.
     bool dense = false;
     int64_t *acc = nullptr;
     int64_t *acc_off = nullptr;
+    int32_t *acc_lab = nullptr;
+    int64_t acc_total = 0;  // entries of acc
     int acc_shift = 0;
 
     // counters and step scratch

@@ -435,32 +435,45 @@ __global__ void __launch_bounds__(1024) k_sum_inst(const int32_t *inst_k, const 
 
 // ---------------- u2-u4, dense accumulator form ----------------
 //
-// Cluster sums in fixed point: every member value x of a recomputed cluster
-// adds ceil(x * 2^shift) to the cluster's accumulator entry of its term with
-// an integer atomic. Integer sums do not depend on the order of the adds, so
-// the result is deterministic; it exceeds the exact sum by less than one unit
-// 2^-shift per member. The rows are then read in ascending term order.
+// Cluster sums in fixed point: every member value x contributes
+// q(x) = ceil(x * 2^shift) to the cluster's accumulator entry of its term.
+// The accumulator is kept across steps and updated incrementally: an object
+// whose label differs from the one it was last added under (acc_lab) has its
+// q values subtracted from the old cluster and added to the new one, with
+// integer atomics. Integer sums do not depend on the order of the adds, so
+// every entry equals the sum of q over the cluster's current members exactly,
+// whatever the history; it exceeds the exact sum by less than one unit
+// 2^-shift per member. The clusters touched are exactly the moving ones; their
+// rows are then read in ascending term order.
 
 __global__ void k_label_counts(int64_t N, const int32_t *labels, int64_t *cnt) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
         atomicAdd(reinterpret_cast<unsigned long long *>(cnt + labels[i]), 1ull);
 }
 
-// One warp per object of a recomputed cluster: its values into the cluster's row.
-__global__ void k_acc_scatter(int64_t N, const int32_t *labels, const int64_t *flag, const int64_t *row_ptr,
+// One warp per object whose label changed since it was last added: its q
+// values move from the old cluster's row to the new one's.
+__global__ void k_acc_scatter(int64_t N, const int32_t *labels, int32_t *acc_lab, const int64_t *row_ptr,
                               const int32_t *idx, const float *val, const int32_t *clu_doff, const int64_t *acc_off,
                               float fscale, int64_t *acc, int64_t *moved) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     long long mv = 0;
     for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < N; i += nw) {
-        const int32_t j = labels[i];
-        if (!flag[j]) continue;
+        const int32_t jn = labels[i], jo = acc_lab[i];
+        if (jn == jo) continue;
         const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
-        unsigned long long *row = reinterpret_cast<unsigned long long *>(acc + acc_off[j] - clu_doff[j]);
-        for (int64_t h = rb + lane; h < re; h += 32)
-            atomicAdd(row + idx[h], (unsigned long long)__float2ll_ru(val[h] * fscale));
-        mv += re - rb;
+        unsigned long long *rn = reinterpret_cast<unsigned long long *>(acc + acc_off[jn] - clu_doff[jn]);
+        unsigned long long *ro =
+            jo >= 0 ? reinterpret_cast<unsigned long long *>(acc + acc_off[jo] - clu_doff[jo]) : nullptr;
+        for (int64_t h = rb + lane; h < re; h += 32) {
+            const unsigned long long q = (unsigned long long)__float2ll_ru(val[h] * fscale);
+            atomicAdd(rn + idx[h], q);
+            if (ro) atomicAdd(ro + idx[h], 0ull - q);  // two's complement: subtracts q
+        }
+        mv += (re - rb) * (jo >= 0 ? 2 : 1);
+        __syncwarp();
+        if (lane == 0) acc_lab[i] = jn;
     }
     if (lane == 0 && mv) atomicAdd(reinterpret_cast<unsigned long long *>(moved), (unsigned long long)mv);
 }
@@ -526,16 +539,16 @@ __global__ void __launch_bounds__(WR_THREADS) k_acc_rows1(
 }
 
 // Pass 2, one CTA per cluster: the new row in ascending term order (block
-// compaction of the non-zero entries), u = s / ||s|| as FP32, and the
-// accumulator row cleared for the next step. Other clusters copy their row.
+// compaction of the non-zero entries) and u = s * (2^-shift / ||s||) as FP32.
+// Other clusters copy their row.
 __global__ void __launch_bounds__(WR_THREADS) k_acc_rows2(
-    int32_t k, const int64_t *flag, const int64_t *acc_off, const int32_t *clu_doff, int64_t *acc,
+    int32_t k, const int64_t *flag, const int64_t *acc_off, const int32_t *clu_doff, const int64_t *acc,
     double inv_scale, const int64_t *coff_old, const int32_t *cterm_old, const float *cval_old,
     const double *snorm_new, const int64_t *coff_new, int32_t *cterm_new, float *cval_new, int32_t *cclu_new,
     int64_t cap, unsigned long long *error) {
-    constexpr int PER = 4;  // entries per thread and chunk
+    constexpr int PER = 4;  // sub-chunks of WR_THREADS entries per chunk
     constexpr int NWR = WR_THREADS / 32;
-    __shared__ int warp_n[NWR];
+    __shared__ int warp_n[PER][NWR];
     const int j = blockIdx.x;
     if (j >= k) return;
     const bool over = coff_new[k] > cap;  // more entries than the buffers hold: write nothing, report
@@ -553,46 +566,45 @@ __global__ void __launch_bounds__(WR_THREADS) k_acc_rows2(
     }
     const int64_t base = acc_off[j], L = acc_off[j + 1] - base;
     const int32_t doff = clu_doff[j];
-    const double nrm = snorm_new[j];
+    const double f = inv_scale / snorm_new[j];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
     int64_t o = o0;
     for (int64_t c0 = 0; c0 < L; c0 += (int64_t)WR_THREADS * PER) {
-        // thread tid takes entries c0 + tid*PER .. +PER-1: ascending in tid
+        // sub-chunk m holds entries c0 + m*WR_THREADS + tid (coalesced loads)
         long long v[PER];
-        int n = 0;
+        unsigned bal[PER];
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
-            const int64_t t = c0 + (int64_t)threadIdx.x * PER + m;
+            const int64_t t = c0 + (int64_t)m * WR_THREADS + threadIdx.x;
             v[m] = t < L ? acc[base + t] : 0;
-            n += v[m] != 0;
+            bal[m] = __ballot_sync(0xffffffffu, v[m] != 0);
         }
-        int inc = n;
+        if (lane == 0) {
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, inc, d);
-            if (lane >= d) inc += y;
+            for (int m = 0; m < PER; ++m) warp_n[m][warp] = __popc(bal[m]);
         }
-        if (lane == 31) warp_n[warp] = inc;
         __syncthreads();
-        int before = 0, total = 0;
+        // entries before (m, warp): all of sub-chunks < m, warps < warp of m
+        int total = 0;
 #pragma unroll
-        for (int w = 0; w < NWR; ++w) {
-            const int x = warp_n[w];
-            before += w < warp ? x : 0;
-            total += x;
-        }
-        int64_t p = o + before + (inc - n);
+        for (int m = 0; m < PER; ++m)
+#pragma unroll
+            for (int w = 0; w < NWR; ++w) total += warp_n[m][w];
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
             if (v[m]) {
-                const int64_t t = c0 + (int64_t)threadIdx.x * PER + m;
+                int pre = 0;
+                for (int mm = 0; mm < m; ++mm)
+                    for (int w = 0; w < NWR; ++w) pre += warp_n[mm][w];
+                for (int w = 0; w < warp; ++w) pre += warp_n[m][w];
+                const int64_t p = o + pre + __popc(bal[m] & below);
+                const int64_t t = c0 + (int64_t)m * WR_THREADS + threadIdx.x;
                 if (!over) {
                     cterm_new[p] = (int32_t)t + doff;
-                    cval_new[p] = (float)((double)v[m] * inv_scale / nrm);
+                    cval_new[p] = (float)((double)v[m] * f);
                     cclu_new[p] = j;
                 }
-                acc[base + t] = 0;
-                ++p;
             }
         }
         o += total;
@@ -740,6 +752,10 @@ cudaError_t reseed_dev(sivf_ctx *c, const int32_t *init_ids_dev) {
     SIVF_CUDA_TRY(cudaMemsetAsync(c->lam_prev, 0, k, c->stream));
     SIVF_CUDA_TRY(cudaMemsetAsync(c->moving, 1, k, c->stream));
     SIVF_CUDA_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream));
+    if (c->dense) {  // no member has been added yet
+        SIVF_CUDA_TRY(cudaMemsetAsync(c->acc, 0, sizeof(int64_t) * (size_t)c->acc_total, c->stream));
+        SIVF_CUDA_TRY(cudaMemsetAsync(c->acc_lab, 0xFF, sizeof(int32_t) * N, c->stream));
+    }
     c->iter = 1;  // finalize below marks every cluster moving
     SIVF_CUDA_TRY(launch_finalize_assign(c));
     c->iter = 0;
@@ -804,8 +820,8 @@ cudaError_t run_update_dense(sivf_ctx *c) {
     k_recompute_flags<<<blocks_for(k), TPB, 0, s>>>(k, c->lam, cnt, flag);
     const float fscale = ldexpf(1.0f, c->acc_shift);
     const double inv_scale = ldexp(1.0, -c->acc_shift);
-    k_acc_scatter<<<blocks_for(N * 32), TPB, 0, s>>>(N, c->labels, flag, c->row_ptr, c->idx, c->val, c->clu_doff,
-                                                     c->acc_off, fscale, c->acc, moved_d);
+    k_acc_scatter<<<blocks_for(N * 32), TPB, 0, s>>>(N, c->labels, c->acc_lab, c->row_ptr, c->idx, c->val,
+                                                     c->clu_doff, c->acc_off, fscale, c->acc, moved_d);
     k_acc_rows1<<<(unsigned)k, WR_THREADS, 0, s>>>(k, flag, cnt, c->acc_off, c->clu_doff, c->acc, inv_scale,
                                                    c->coff[cur], c->cterm[cur], c->cval[cur], c->snorm, sz,
                                                    c->snorm_new, jAd, jUd);
