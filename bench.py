@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2", choices=sorted(CONFIGS) + ["c4"])
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "fp16"])
-    ap.add_argument("--icp", type=int, default=1)
+    ap.add_argument("--icp", type=int, default=1, choices=[0, 1, 2],
+                    help="1: SIVF (Algorithm 4); 0: unfiltered IVF (Algorithm 2); 2: IVF-CBICP (Algorithm 3)")
     ap.add_argument("--max-iter", type=int, default=None)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
@@ -183,11 +184,12 @@ def sum_over_ranks(x, world):
     return float(t.item())
 
 
-def cpu_baseline(w, c, ini, iters):
+def cpu_baseline(w, c, ini, iters, icp=1):
     """The FP64 oracle (OpenMP, all host cores) on a bounded sample of the same
-    workload: the first `iters` Lloyd iterations (assign + update)."""
+    workload: the first `iters` Lloyd iterations (assign + update), in the
+    same assignment algorithm."""
     from oracle import Oracle
-    o = Oracle(c, w.k, ini, icp=True)
+    o = Oracle(c, w.k, ini, icp=icp)
     t0 = time.perf_counter()
     done = 0
     for _ in range(iters):
@@ -211,7 +213,7 @@ def run_reference(args, w):
     from oracle import Oracle
     c = generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, w.seed)
     ini = init_ids(w.N, w.k, w.init_seed)
-    o = Oracle(c, w.k, ini, icp=bool(args.icp))
+    o = Oracle(c, w.k, ini, icp=args.icp)
 
     def step():
         a = o.assign()
@@ -252,7 +254,7 @@ def run_batched(args):
     ws = batched_instances(64, max_iter=args.max_iter or 50)
     cs = [generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, w.seed) for w in ws]
     inis = [init_ids(w.N, w.k, w.init_seed) for w in ws]
-    b = SIVFBatch(cs, [w.k for w in ws], inis, precision=prec, icp=bool(args.icp), threads=args.threads,
+    b = SIVFBatch(cs, [w.k for w in ws], inis, precision=prec, icp=args.icp, threads=args.threads,
                   ctas_per_sm=args.ctas_per_sm, use_graph=bool(args.graph), autotune=bool(args.autotune))
     gini = np.ascontiguousarray(np.concatenate([ini + off for ini, off in
                                                 zip(inis, np.cumsum([0] + [w.N for w in ws[:-1]]))]), dtype=np.int32)
@@ -322,7 +324,7 @@ def main():
     c = generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, w.seed)
     ini = init_ids(w.N, w.k, w.init_seed)
     dev = torch.device("cuda", torch.cuda.current_device())
-    g = SIVF(c.row_ptr, c.idx, c.val, c.D, w.k, ini, precision=w.precision, icp=bool(args.icp),
+    g = SIVF(c.row_ptr, c.idx, c.val, c.D, w.k, ini, precision=w.precision, icp=args.icp,
              threads=args.threads, ctas_per_sm=args.ctas_per_sm, use_graph=bool(args.graph),
              autotune=bool(args.autotune))
     stream = torch.cuda.current_stream()
@@ -413,7 +415,7 @@ def main():
         e_iters = 0
         E = max(1, min(args.steps, 3))
         for _ in range(E):
-            ge = SIVF(rp, ix, vl, c.D, w.k, ini, precision=w.precision, icp=bool(args.icp),
+            ge = SIVF(rp, ix, vl, c.D, w.k, ini, precision=w.precision, icp=args.icp,
                       threads=args.threads, ctas_per_sm=args.ctas_per_sm, use_graph=bool(args.graph),
                       autotune=bool(args.autotune), inputs_on_host=True)
             it, _ = ge.run(w.max_iter)
@@ -427,7 +429,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, c, ini, args.cpu_sample_iters)
+        cpu = cpu_baseline(w, c, ini, args.cpu_sample_iters, args.icp)
 
     if rank == 0:
         line = {
@@ -438,7 +440,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": f"{w.name}: N={w.N} D={w.D} nnz={c.nnz} k={w.k} zipf={w.zipf_s} "
                                    f"len=lognormal({w.mu:.3f},{w.sigma}) clip[{w.lo},{w.hi}] seed={w.seed}",
-                       "precision": w.precision, "icp": bool(args.icp), "max_iter": w.max_iter,
+                       "precision": w.precision, "icp": ["ivf", "sivf", "ivf-cbicp"][args.icp], "max_iter": w.max_iter,
                        "iters_per_step": iters_per_step, "sec_per_iter": ms / 1e3 / tot_iters,
                        "l2": f"inputs larger than L2: every assignment streams the object CSR "
                              f"({(c.nnz * 8 + (w.N + 1) * 8) / 1e9:.2f} GB); the inverted file is reused from L2 "

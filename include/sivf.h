@@ -53,7 +53,11 @@ typedef enum { SIVF_FP32 = 0, SIVF_BF16 = 1, SIVF_FP16 = 2 } sivf_precision;
 
 typedef struct {
     sivf_precision prec; /* posting value precision for the scan */
-    int icp;             /* 1: ICP filter (Algorithm 4); 0: unfiltered (Algorithm 2) */
+    int icp;             /* 1: SIVF with the ICP filter (Algorithm 4); 0: unfiltered
+                            (Algorithm 2); 2: IVF-CBICP (Algorithm 3), the paper's
+                            branch-based baseline over an unstructured file (ascending
+                            centroid ids in every list, mf0 = list length), kept for
+                            ablation: 128 threads, shared score vector, no tuning */
     int threads;         /* threads per CTA of the assignment kernel (32, 64, 128, 256 or
                             512); 0 = automatic */
     int ctas_per_sm;     /* resident CTAs per SM of the assignment kernel; 0 = automatic */

@@ -14,6 +14,10 @@
  *   icp = 1 : SIVF assignment (Algorithm 4): if the object's cluster was
  *             invariant at the previous iteration, only the front (moving)
  *             segment of each posting list is scanned.
+ *   icp = 2 : IVF-CBICP assignment (Algorithm 3): the same objects are
+ *             filtered, but they traverse every posting of each list and a
+ *             second branch, per posting, skips the invariant centroids. It
+ *             reaches the same scores and labels; only the traversal differs.
  * The update step (Algorithm 5) is shared by both modes and always lays the
  * inverted file out in the structured form (moving centroids in front,
  * invariant centroids behind, ascending centroid id inside each part).
@@ -129,7 +133,7 @@ void orc_destroy(orc *o) {
 /* Iteration 0: mu_j^[0] = x_{init_ids[j]} (Algorithm 1 input M^[0]). */
 orc *orc_create(int64_t N, int32_t D, int32_t k, const int64_t *row_ptr, const int32_t *idx,
                 const float *val, const int32_t *init_ids, int icp) {
-    if (N < 1 || D < 1 || k < 1 || (int64_t)k > N) return NULL;
+    if (N < 1 || D < 1 || k < 1 || (int64_t)k > N || icp < 0 || icp > 2) return NULL;
     orc *o = (orc *)xcalloc(1, sizeof(orc));
     if (!o) return NULL;
     o->N = N; o->D = D; o->k = k;
@@ -171,9 +175,10 @@ orc *orc_create(int64_t N, int32_t D, int32_t k, const int64_t *row_ptr, const i
 
 /*
  * Assignment step at iteration r (Algorithm 2 when icp = 0, Algorithm 4 when
- * icp = 1). stats[0..7] = changed, n_moving (lambda^[r] = 0 count), sim-calcs,
- * postings visited, objective sum_i rho_{i,a(i)}, filtered objects,
- * n_moving at r-1, iteration r.
+ * icp = 1, Algorithm 3 when icp = 2). stats[0..7] = changed, n_moving
+ * (lambda^[r] = 0 count), sim-calcs, postings visited (traversed, whether or
+ * not accumulated), objective sum_i rho_{i,a(i)}, filtered objects, n_moving at
+ * r-1, iteration r.
  */
 int orc_assign(orc *o, double *stats) {
     const int64_t N = o->N;
@@ -202,6 +207,14 @@ int orc_assign(orc *o, double *stats) {
                 int32_t s = o->idx[h];
                 double v = (double)o->val[h];
                 int64_t b = o->if_off[s];
+                if (filt && o->icp == 2) {
+                    /* Algorithm 3: every posting, a branch on lambda of its centroid */
+                    int64_t e = o->if_off[s + 1];
+                    for (int64_t q = b; q < e; ++q)
+                        if (o->lambda[o->if_cid[q]] == 0) rho[o->if_cid[q]] += v * o->if_u[q];
+                    postings += e - b;
+                    continue;
+                }
                 int64_t e = filt ? b + o->if_mf0[s] : o->if_off[s + 1];
                 for (int64_t q = b; q < e; ++q) rho[o->if_cid[q]] += v * o->if_u[q];
                 postings += e - b;

@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY (see package docstring).
 
 Paper map (Aoyama & Saito, arXiv 2103.16141):
-  Oracle.assign()  -> Algorithm 2 (icp=False) / Algorithm 4 (icp=True)
+  Oracle.assign()  -> Algorithm 2 (icp=False) / Algorithm 4 (icp=True) /
+                      Algorithm 3 (icp="cbicp")
   Oracle.update()  -> Algorithm 5 (means, unit length, structured inverted file)
   Oracle.run()     -> Algorithm 1 loop until no label changes
 """
@@ -104,7 +105,9 @@ class Oracle:
     """One clustering instance held by the C oracle. Arrays passed in are kept
     referenced for the lifetime of the object (the C side borrows them)."""
 
-    def __init__(self, corpus, k: int, init_ids: np.ndarray, icp: bool = True, threads: int = 0, lib=None):
+    def __init__(self, corpus, k: int, init_ids: np.ndarray, icp=True, threads: int = 0, lib=None):
+        """icp: False/0 unfiltered (Algorithm 2), True/1 SIVF (Algorithm 4),
+        2 or "cbicp" IVF-CBICP (Algorithm 3)."""
         self._lib = lib if lib is not None else _load()
         if threads:
             self._lib.orc_set_threads(int(threads))
@@ -115,11 +118,12 @@ class Oracle:
         init = np.ascontiguousarray(init_ids, dtype=np.int32)
         if init.shape != (self.k,):
             raise ValueError("init_ids must have k entries")
+        mode = 2 if (icp == "cbicp" or (not isinstance(icp, bool) and icp == 2)) else int(bool(icp))
         self._h = self._lib.orc_create(self.N, self.D, self.k, _p(self._row_ptr), _p(self._idx),
-                                       _p(self._val), _p(init), int(bool(icp)))
+                                       _p(self._val), _p(init), mode)
         if not self._h:
             raise ValueError("oracle: invalid arguments or out of memory")
-        self.icp = bool(icp)
+        self.icp = mode
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -80,6 +80,10 @@ void pick_assign_config(sivf_ctx *c) {
     cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const bool fits = ((size_t)((c->kmax + 3) & ~3) * 4 + (size_t)T * ASSIGN_STAGE_BYTES) <= (size_t)smem;
     c->assign_global = c->cfg.score_buffer == 2 || (c->cfg.score_buffer == 0 && !fits) ? 1 : 0;
+    if (c->cfg.icp == 2) {  // IVF-CBICP: 128 threads, shared score vector, no tuning
+        c->assign_threads = 128;
+        c->assign_global = 0;
+    }
 }
 
 }  // namespace
@@ -149,6 +153,17 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
     INIT_CUDA(cudaGetDevice(&c->device), "cudaGetDevice");
     INIT_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device), "attr");
     pick_assign_config(c);
+    if (c->cfg.icp == 2) {  // the IVF-CBICP kernel keeps the score vector and lambda bits in shared memory
+        int smem = 0;
+        INIT_CUDA(cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device), "attr");
+        const size_t need = (size_t)((c->kmax + 3) & ~3) * 4 + 128 * (size_t)ASSIGN_STAGE_BYTES +
+                            (size_t)((k + 31) >> 5) * 4;
+        if (need > (size_t)smem) {
+            free_all(c);
+            delete c;
+            return SIVF_ERR_INVALID_ARG;
+        }
+    }
     // nnz from row_ptr[N]
     int64_t nnz = 0, first = 0;
     INIT_CUDA(cudaMemcpyAsync(&nnz, row_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream), "read nnz");
@@ -361,7 +376,8 @@ sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t
     if (N < 1 || N > 0x7FFFFFFFll || D < 1 || D > (1 << 30) || k < 1 || (int64_t)k > N || !row_ptr || !idx || !val ||
         !init_ids)
         return SIVF_ERR_INVALID_ARG;
-    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16)) return SIVF_ERR_INVALID_ARG;
+    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16 || cfg->icp < 0 || cfg->icp > 2))
+        return SIVF_ERR_INVALID_ARG;
     if (!distinct_ids(init_ids, k, N)) return SIVF_ERR_INVALID_ARG;
     if (cfg && cfg->inputs_on_host) {
         // host CSR: copy it into device buffers that the context adopts
@@ -403,7 +419,8 @@ sivf_status sivf_batch_init(sivf_ctx **out, const sivf_config *cfg, int32_t n_in
     if (!out) return SIVF_ERR_INVALID_ARG;
     *out = nullptr;
     if (n_inst < 1 || n_inst > 65536 || !descs) return SIVF_ERR_INVALID_ARG;
-    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16 || cfg->inputs_on_host)) return SIVF_ERR_INVALID_ARG;
+    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16 || cfg->inputs_on_host || cfg->icp < 0 || cfg->icp > 2))
+        return SIVF_ERR_INVALID_ARG;
     std::vector<int64_t> inst_obj(1, 0);
     std::vector<int32_t> inst_k(1, 0), inst_d(1, 0);
     for (int32_t m = 0; m < n_inst; ++m) {
@@ -667,7 +684,7 @@ sivf_status sivf_assign(sivf_ctx *c, int64_t *n_changed) {
         return fail(c, SIVF_ERR_STATE,
                     "sivf_update must run between two assignments (and after sivf_set_labels)");
     c->iter += 1;
-    if (c->cfg.autotune && !c->tuned && c->iter == 2) API_CUDA(c, autotune_assign(c), "autotune");
+    if (c->cfg.autotune && c->cfg.icp != 2 && !c->tuned && c->iter == 2) API_CUDA(c, autotune_assign(c), "autotune");
     API_CUDA(c, enqueue_assign(c, true), "assignment");
     API_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
     float ms = 0.f;

@@ -335,8 +335,12 @@ __device__ __forceinline__ void rho_zero(uint32_t *p) {
 // GRHO: the score vector lives in global memory (a kmax slab per CTA, L2
 // atomics) instead of shared memory; slower per posting, but independent of
 // the shared-memory size, so it serves any k and lets more CTAs reside.
-template <int T, int PREC, bool CID16, bool GRHO>
-__global__ void __launch_bounds__(T, assign_min_blocks<T>()) assign_kernel(AssignParams P) {
+// CB: IVF-CBICP (Algorithm 3) instead of SIVF (Algorithm 4). A filtered
+// object then traverses every posting of an unstructured file (ascending
+// centroid ids) and a per-posting branch on lambda^[r-1] skips the invariant
+// centroids; the scores and labels are the same.
+template <int T, int PREC, bool CID16, bool GRHO, bool CB = false>
+__global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_kernel(AssignParams P) {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int NW = T / 32;
     const int kpad = (P.kmax + 3) & ~3;
@@ -348,6 +352,7 @@ __global__ void __launch_bounds__(T, assign_min_blocks<T>()) assign_kernel(Assig
     int *s_len = reinterpret_cast<int *>(s_seg + T);
     int *s_item = s_len + T;
     int *s_rend = s_item + T;
+    uint32_t *s_lam = reinterpret_cast<uint32_t *>(s_rend + T);  // CB: lambda^[r-1] bits of all clusters
     __shared__ int2 warp_i2[32];
     __shared__ int2 s_total2;
     __shared__ long long s_obj;
@@ -360,6 +365,13 @@ __global__ void __launch_bounds__(T, assign_min_blocks<T>()) assign_kernel(Assig
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int j = tid; j < kpad; j += T) rho_zero<GRHO>(rho + j);
+    if constexpr (CB) {
+        const int nbits = ((P.k + 31) >> 5) << 5;
+        for (int j = tid; j < nbits; j += T) {  // a warp covers 32 consecutive clusters
+            const unsigned b = __ballot_sync(0xffffffffu, j < P.k && P.lam_prev[j] != 0);
+            if (lane == 0) s_lam[j >> 5] = b;
+        }
+    }
     // per-CTA counters in shared memory (written by one thread or by lane 0
     // of each warp): filtered, sim-calcs, changed, re-scored, re-score candidates
     __shared__ unsigned long long s_cnt[5];
@@ -392,6 +404,12 @@ __global__ void __launch_bounds__(T, assign_min_blocks<T>()) assign_kernel(Assig
         const int mb = P.mov_beg[inst];
         const int n_mov = filt ? P.mov_beg[inst + 1] - mb : 0;
         const int32_t *movs = P.mov_list + mb;
+        // rho[id] += q; under CB a filtered object skips invariant centroids
+        const bool cbf = CB && filt;
+        auto add = [&](int id, float prod) {
+            if (!cbf || !((s_lam[(k_off + id) >> 5] >> ((k_off + id) & 31)) & 1u))
+                atomicAdd(&rho[id], __float2uint_ru(prod));
+        };
 
         // ---- similarity scan (Algorithm 4, lines 7-13) ----
         // The object's terms are staged T at a time. Each segment (the part of
@@ -418,7 +436,7 @@ __global__ void __launch_bounds__(T, assign_min_blocks<T>()) assign_kernel(Assig
                 const int t = P.idx[cb + tid];
                 const int64_t o0 = P.if_off[t];
                 const int lfull = (int)(P.if_off[t + 1] - o0);
-                const int len = filt ? P.if_mf0[t] : lfull;
+                const int len = (filt && !CB) ? P.if_mf0[t] : lfull;
                 const int fb = lfull & ~(SC_BLK - 1);
                 const int r0 = min(len, fb) & ~(SC_BLK - 1);  // postings in full, fully scanned blocks
                 const float vs = P.val[cb + tid] * FIX_SCALE;  // exact: power-of-two scaling
@@ -460,13 +478,13 @@ __global__ void __launch_bounds__(T, assign_min_blocks<T>()) assign_kernel(Assig
                             const Post4 a = load_tiled<PREC, CID16>(P, pos);
                             const Post4 b = load_tiled<PREC, CID16>(P, pos + SC_BLK);
 #pragma unroll
-                            for (int m = 0; m < 4; ++m) atomicAdd(&rho[a.id[m]], __float2uint_ru(vs * a.u[m]));
+                            for (int m = 0; m < 4; ++m) add(a.id[m], vs * a.u[m]);
 #pragma unroll
-                            for (int m = 0; m < 4; ++m) atomicAdd(&rho[b.id[m]], __float2uint_ru(vs * b.u[m]));
+                            for (int m = 0; m < 4; ++m) add(b.id[m], vs * b.u[m]);
                         } else if (off < r0) {  // the segment's odd last full block
                             const Post4 a = load_tiled<PREC, CID16>(P, sb + off + 4 * lane);
 #pragma unroll
-                            for (int m = 0; m < 4; ++m) atomicAdd(&rho[a.id[m]], __float2uint_ru(vs * a.u[m]));
+                            for (int m = 0; m < 4; ++m) add(a.id[m], vs * a.u[m]);
                         } else {  // a remainder of RMIN .. 127 postings, starting at r0
                             const int rem = s_len[h] - r0;
                             if (r0 < fb) {
@@ -474,7 +492,7 @@ __global__ void __launch_bounds__(T, assign_min_blocks<T>()) assign_kernel(Assig
                                 const Post4 a = load_tiled<PREC, CID16>(P, sb + r0 + 4 * lane);
 #pragma unroll
                                 for (int m = 0; m < 4; ++m)
-                                    if (32 * m + lane < rem) atomicAdd(&rho[a.id[m]], __float2uint_ru(vs * a.u[m]));
+                                    if (32 * m + lane < rem) add(a.id[m], vs * a.u[m]);
                             } else {  // the ragged tail, canonical order
                                 int id[4];
                                 float u[4];
@@ -483,7 +501,7 @@ __global__ void __launch_bounds__(T, assign_min_blocks<T>()) assign_kernel(Assig
                                     if (32 * m + lane < rem) load_one<PREC, CID16>(P, sb + r0 + 32 * m + lane, id[m], u[m]);
 #pragma unroll
                                 for (int m = 0; m < 4; ++m)
-                                    if (32 * m + lane < rem) atomicAdd(&rho[id[m]], __float2uint_ru(vs * u[m]));
+                                    if (32 * m + lane < rem) add(id[m], vs * u[m]);
                             }
                         }
                     }
@@ -524,7 +542,7 @@ __global__ void __launch_bounds__(T, assign_min_blocks<T>()) assign_kernel(Assig
                         }
 #pragma unroll
                         for (int m = 0; m < RU; ++m)
-                            if (ok[m]) atomicAdd(&rho[id[m]], __float2uint_ru(vv[m] * u[m]));
+                            if (ok[m]) add(id[m], vv[m] * u[m]);
                     }
                 }
             }
@@ -704,11 +722,12 @@ __global__ void __launch_bounds__(1024) finalize_kernel(int32_t k, int first_ite
     }
 }
 
-template <int T, int PREC, bool CID16, bool GRHO>
+template <int T, int PREC, bool CID16, bool GRHO, bool CB = false>
 cudaError_t launch_t(sivf_ctx *c, const AssignParams &P, int ctas_per_sm) {
     const int kpad = (c->kmax + 3) & ~3;
-    const size_t smem = (GRHO ? 0 : (size_t)kpad * 4) + (size_t)T * ASSIGN_STAGE_BYTES;
-    auto kern = assign_kernel<T, PREC, CID16, GRHO>;
+    const size_t smem = (GRHO ? 0 : (size_t)kpad * 4) + (size_t)T * ASSIGN_STAGE_BYTES +
+                        (CB ? (size_t)((c->k + 31) >> 5) * 4 : 0);
+    auto kern = assign_kernel<T, PREC, CID16, GRHO, CB>;
     // the attribute and occupancy queries are host calls that a stream capture
     // refuses: they run on the first (host-launched) step and are cached
     if (c->assign_grid <= 0) {
@@ -741,6 +760,9 @@ cudaError_t launch_prec(sivf_ctx *c, const AssignParams &P) {
 template <int PREC>
 cudaError_t launch_ids(sivf_ctx *c, const AssignParams &P) {
     const bool ids16 = P.sc_id16 || P.sc_pack;
+    if (c->cfg.icp == 2)  // IVF-CBICP ablation: one configuration
+        return ids16 ? launch_t<128, PREC, true, false, true>(c, P, c->assign_ctas_per_sm)
+                     : launch_t<128, PREC, false, false, true>(c, P, c->assign_ctas_per_sm);
     if (c->assign_global)
         return ids16 ? launch_prec<PREC, true, true>(c, P) : launch_prec<PREC, false, true>(c, P);
     return ids16 ? launch_prec<PREC, true, false>(c, P) : launch_prec<PREC, false, false>(c, P);

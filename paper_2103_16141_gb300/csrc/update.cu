@@ -614,11 +614,13 @@ __global__ void __launch_bounds__(WR_THREADS) k_acc_rows2(
 
 // ---------------- u5: structured inverted file ----------------
 
+// key = term << 1 | part (0 = front, moving; 1 = back, invariant). The
+// unstructured file of IVF-CBICP keeps every posting in part 0.
 __global__ void k_if_keys(const int64_t *n_dev, int64_t cap, const int32_t *cterm, const int32_t *cclu,
-                          const uint8_t *lam, uint32_t *keys, uint32_t *vals, uint32_t *cnt2) {
+                          const uint8_t *lam, int structured, uint32_t *keys, uint32_t *vals, uint32_t *cnt2) {
     const int64_t n = min(*n_dev, cap);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t key = ((uint32_t)cterm[e] << 1) | (uint32_t)(lam[cclu[e]] ? 1 : 0);
+        const uint32_t key = ((uint32_t)cterm[e] << 1) | (uint32_t)(structured && lam[cclu[e]] ? 1 : 0);
         keys[e] = key;
         vals[e] = (uint32_t)e;
         atomicAdd(cnt2 + key, 1u);
@@ -781,7 +783,8 @@ cudaError_t build_inverted_file(sivf_ctx *c) {
     uint32_t *k1 = ws.take<uint32_t>((size_t)cap + 1), *v1 = ws.take<uint32_t>((size_t)cap + 1);
     if (!cnt2 || !len || !slen || !total || !k0 || !v0 || !k1 || !v1) return cudaErrorMemoryAllocation;
     SIVF_CUDA_TRY(cudaMemsetAsync(cnt2, 0, sizeof(uint32_t) * 2 * c->D, c->stream));
-    k_if_keys<<<blocks_for(cap), TPB, 0, c->stream>>>(n_dev, cap, c->cterm[cur], c->cclu, c->lam, k0, v0, cnt2);
+    k_if_keys<<<blocks_for(cap), TPB, 0, c->stream>>>(n_dev, cap, c->cterm[cur], c->cclu, c->lam,
+                                                      c->cfg.icp == 2 ? 0 : 1, k0, v0, cnt2);
     k_if_lens<<<blocks_for(c->D), TPB, 0, c->stream>>>(c->D, cnt2, len, slen, c->if_mf0);
     note_launch(2);
     SIVF_CUDA_TRY(cudaGetLastError());

@@ -20,6 +20,14 @@ SCORE_BUFFERS = {"auto": 0, "shared": 1, "global": 2}
 UPDATE_MODES = {"auto": 0, "dense": 1, "sort": 2}
 
 
+def icp_mode(icp) -> int:
+    """False/0: unfiltered (Algorithm 2); True/1: SIVF (Algorithm 4);
+    2 or "cbicp": IVF-CBICP (Algorithm 3)."""
+    if icp == "cbicp" or (not isinstance(icp, bool) and icp == 2):
+        return 2
+    return int(bool(icp))
+
+
 class sivf_config(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("icp", ctypes.c_int), ("threads", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("mem_cap_bytes", ctypes.c_int64), ("use_graph", ctypes.c_int),
@@ -202,7 +210,7 @@ class SIVF:
     buffers of its own.
     """
 
-    def __init__(self, row_ptr, idx, val, D: int, k: int, init_ids, precision: str = "fp32", icp: bool = True,
+    def __init__(self, row_ptr, idx, val, D: int, k: int, init_ids, precision: str = "fp32", icp=True,
                  threads: int = 0, ctas_per_sm: int = 0, mem_cap_bytes: int = 0, stream=None, use_graph: bool = False,
                  autotune: bool = False, score_buffer: str = "auto", inputs_on_host: bool = False,
                  update_mode: str = "auto"):
@@ -240,7 +248,7 @@ class SIVF:
         self.D, self.k = int(D), int(k)
         ini = np.ascontiguousarray(np.asarray(init_ids, dtype=np.int32))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        cfg = sivf_config(PRECISIONS[precision], int(bool(icp)), int(threads), int(ctas_per_sm), int(mem_cap_bytes),
+        cfg = sivf_config(PRECISIONS[precision], icp_mode(icp), int(threads), int(ctas_per_sm), int(mem_cap_bytes),
                           int(bool(use_graph)), int(bool(autotune)), SCORE_BUFFERS[score_buffer],
                           UPDATE_MODES[update_mode], int(bool(inputs_on_host)))
         self.ctx = sivf_init(cfg, self.N, self.D, self.k, rp_p, ix_p, vl_p, ini.ctypes.data, self.stream.cuda_stream)
@@ -359,7 +367,7 @@ class SIVFBatch:
     ks: clusters per instance; init_ids: per-instance local seed ids.
     """
 
-    def __init__(self, corpora, ks, init_ids, precision: str = "fp32", icp: bool = True, threads: int = 0,
+    def __init__(self, corpora, ks, init_ids, precision: str = "fp32", icp=True, threads: int = 0,
                  ctas_per_sm: int = 0, use_graph: bool = False, autotune: bool = False, score_buffer: str = "auto",
                  update_mode: str = "auto"):
         import numpy as np
@@ -379,7 +387,7 @@ class SIVFBatch:
         self.n_inst = len(descs)
         self.Ns = [d.N for d in descs]
         self.ks = [int(k) for k in ks]
-        cfg = sivf_config(PRECISIONS[precision], int(bool(icp)), int(threads), int(ctas_per_sm), 0,
+        cfg = sivf_config(PRECISIONS[precision], icp_mode(icp), int(threads), int(ctas_per_sm), 0,
                           int(bool(use_graph)), int(bool(autotune)), SCORE_BUFFERS[score_buffer],
                           UPDATE_MODES[update_mode])
         self.ctx = sivf_batch_init(cfg, descs)

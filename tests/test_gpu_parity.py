@@ -330,3 +330,38 @@ def test_host_inputs_equal_device_inputs():
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_cbicp_lockstep_against_oracle(precision):
+    """IVF-CBICP (Algorithm 3) on the GPU against the oracle in the same mode:
+    labels, filtered objects, sim-calcs and postings traversed."""
+    w = CONFIGS["c2"].scaled(N=8_000, D=1_500, k=500, mu=3.5, hi=400)
+    c, ini = corpus_for(w, seed=43)
+    recs = lockstep(c, w.k, ini, 10, precision=precision, icp="cbicp")
+    assert any(r["stats"]["filtered"] > 0 for r in recs)
+
+
+def test_cbicp_sivf_ivf_three_way_on_gpu():
+    """The three assignment algorithms give the same labels at every
+    iteration; CBICP's sim-calcs equal SIVF's and its postings equal IVF's."""
+    w = CONFIGS["c2"].scaled(N=8_000, D=10_000, k=80)
+    c, ini = corpus_for(w, seed=47)
+    s, v, b = (gpu_instance(c, w.k, ini, icp=m) for m in (True, False, "cbicp"))
+    try:
+        saw_filter = False
+        for _ in range(25):
+            ns, nv, nb = s.assign(), v.assign(), b.assign()
+            assert ns == nv == nb
+            assert np.array_equal(s.labels(), v.labels()) and np.array_equal(b.labels(), v.labels())
+            ss, sv, sb = s.stats(), v.stats(), b.stats()
+            assert sb["simcalc"] == ss["simcalc"] and sb["filtered"] == ss["filtered"]
+            assert sb["postings"] == sv["postings"]
+            saw_filter |= sb["filtered"] > 0
+            if ss["iter"] > 1 and ns == 0:
+                break
+            s.update(), v.update(), b.update()
+        assert saw_filter
+    finally:
+        for g in (s, v, b):
+            g.close()

@@ -27,6 +27,7 @@ MUTANTS = [
      "for (int64_t q = b; q < e; ++q) rho[o->if_cid[q]] += v * o->if_u[q > b ? q - 1 : q];"),
     ("new_cluster_not_marked_moving", "                o->lambda[a1] = 0;\n", "\n"),
     ("update_objective_of_mean", "snorm[j] = sqrt(ss);", "snorm[j] = sqrt(ss) / (double)cnt;"),
+    ("cbicp_branch_inverted", "if (o->lambda[o->if_cid[q]] == 0) rho", "if (o->lambda[o->if_cid[q]] == 1) rho"),
     ("unfiltered_when_invariant", "int filt = o->icp && a_prev >= 0 && o->own_ok[i] && o->lambda[a_prev] == 1;",
      "int filt = o->icp && a_prev >= 0 && o->own_ok[i] && o->lambda[a_prev] == 0;"),
 ]
@@ -42,6 +43,8 @@ def _battery(lib):
     for s in range(4):
         pins.pin_icp_counts(s, lib)
     pins.pin_monotone(21, lib)
+    for s in (3, 4):
+        pins.pin_cbicp(s, lib)
 
 
 def _compile(src_text: str, out_dir: str, name: str):

@@ -271,6 +271,56 @@ def pin_icp_counts(seed, lib=None):
     _check_counts(c, 6, rows)
 
 
+@pytest.mark.parametrize("seed", SMALL_SEEDS)
+def test_cbicp_equals_ivf_labels_and_sivf_simcalcs(seed):
+    """IVF-CBICP (Algorithm 3) traverses every posting like IVF but, for the
+    filtered objects, accumulates only moving centroids like SIVF: its scores
+    and labels equal both at every iteration, its sim-calcs equal SIVF's and
+    its postings traversed equal IVF's."""
+    pin_cbicp(seed)
+
+
+def pin_cbicp(seed, lib=None):
+    X, c, ini = _small(seed, N=60, D=30, k=6)
+    f = Oracle(c, 6, ini, icp=True, lib=lib)
+    g = Oracle(c, 6, ini, icp=False, lib=lib)
+    h = Oracle(c, 6, ini, icp="cbicp", lib=lib)
+    saw_filter = False
+    for _ in range(30):
+        af, ag, ah = f.assign(), g.assign(), h.assign()
+        assert np.array_equal(h.labels(), g.labels())
+        bh, sh, _ = h.scores()
+        bf, sf, _ = f.scores()
+        assert np.array_equal(bh, bf) and np.array_equal(sh, sf)  # best and runner-up, bit for bit
+        assert ah.simcalc == af.simcalc and ah.filtered == af.filtered
+        assert ah.postings == ag.postings
+        assert ah.changed == ag.changed and ah.objective == af.objective
+        saw_filter |= ah.filtered > 0
+        if ah.r > 1 and ah.changed == 0:
+            break
+        f.update(), g.update(), h.update()
+    return saw_filter
+
+
+def test_cbicp_filters_on_c1():
+    w = CONFIGS["c1"]
+    c = generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, w.seed)
+    ini = init_ids(w.N, w.k, w.init_seed)
+    h = Oracle(c, w.k, ini, icp="cbicp")
+    f = Oracle(c, w.k, ini, icp=True)
+    g = Oracle(c, w.k, ini, icp=False)
+    filtered = 0
+    for _ in range(w.max_iter):
+        ah, af, ag = h.assign(), f.assign(), g.assign()
+        assert np.array_equal(h.labels(), f.labels())
+        assert ah.simcalc == af.simcalc and ah.postings == ag.postings
+        filtered += ah.filtered
+        if ah.r > 1 and ah.changed == 0:
+            break
+        h.update(), f.update(), g.update()
+    assert filtered > 0
+
+
 def test_icp_invariant_counts_and_monotone_objective_c1():
     w = CONFIGS["c1"]
     c = generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, w.seed)
