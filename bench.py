@@ -48,8 +48,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2", choices=sorted(CONFIGS) + ["c4"])
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "fp16"])
-    ap.add_argument("--icp", type=int, default=1, choices=[0, 1, 2],
-                    help="1: SIVF (Algorithm 4); 0: unfiltered IVF (Algorithm 2); 2: IVF-CBICP (Algorithm 3)")
+    ap.add_argument("--icp", type=int, default=1, choices=[0, 1, 2, 3],
+                    help="1: SIVF (Algorithm 4); 0: unfiltered IVF (Algorithm 2); 2: IVF-CBICP (Algorithm 3); "
+                         "3: SIVF with the relaxed filter")
     ap.add_argument("--max-iter", type=int, default=None)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
@@ -440,7 +441,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": f"{w.name}: N={w.N} D={w.D} nnz={c.nnz} k={w.k} zipf={w.zipf_s} "
                                    f"len=lognormal({w.mu:.3f},{w.sigma}) clip[{w.lo},{w.hi}] seed={w.seed}",
-                       "precision": w.precision, "icp": ["ivf", "sivf", "ivf-cbicp"][args.icp], "max_iter": w.max_iter,
+                       "precision": w.precision, "icp": ["ivf", "sivf", "ivf-cbicp", "sivf-relaxed"][args.icp], "max_iter": w.max_iter,
                        "iters_per_step": iters_per_step, "sec_per_iter": ms / 1e3 / tot_iters,
                        "l2": f"inputs larger than L2: every assignment streams the object CSR "
                              f"({(c.nnz * 8 + (w.N + 1) * 8) / 1e9:.2f} GB); the inverted file is reused from L2 "

@@ -57,7 +57,14 @@ typedef struct {
                             (Algorithm 2); 2: IVF-CBICP (Algorithm 3), the paper's
                             branch-based baseline over an unstructured file (ascending
                             centroid ids in every list, mf0 = list length), kept for
-                            ablation: 128 threads, shared score vector, no tuning */
+                            ablation: 128 threads, shared score vector, no tuning;
+                            3: SIVF with the relaxed filter (an object whose own
+                            cluster moved also keeps to the moving centroids when its
+                            similarity to its own centroid did not decrease, tested
+                            with the error bound after the front scan; tried while at
+                            most half of its instance's clusters are moving). It pays
+                            off with FP32 postings; with BF16/FP16 the bound is too wide
+                            for the test to pass often */
     int threads;         /* threads per CTA of the assignment kernel (32, 64, 128, 256 or
                             512); 0 = automatic */
     int ctas_per_sm;     /* resident CTAs per SM of the assignment kernel; 0 = automatic */

@@ -18,6 +18,13 @@
  *             filtered, but they traverse every posting of each list and a
  *             second branch, per posting, skips the invariant centroids. It
  *             reaches the same scores and labels; only the traversal differs.
+ *   icp = 3 : SIVF with the relaxed filter the paper cites in Section 3
+ *             (Bottesch et al.): an object whose own cluster moved is also
+ *             restricted to the moving centroids when its similarity to its
+ *             own centroid did not decrease (rho_new >= rho_old; the
+ *             invariant centroids' similarities are unchanged, so none of
+ *             them can overtake it). Tried while at most half of the
+ *             clusters are moving. Same labels, fewer similarities.
  * The update step (Algorithm 5) is shared by both modes and always lays the
  * inverted file out in the structured form (moving centroids in front,
  * invariant centroids behind, ascending centroid id inside each part).
@@ -133,7 +140,7 @@ void orc_destroy(orc *o) {
 /* Iteration 0: mu_j^[0] = x_{init_ids[j]} (Algorithm 1 input M^[0]). */
 orc *orc_create(int64_t N, int32_t D, int32_t k, const int64_t *row_ptr, const int32_t *idx,
                 const float *val, const int32_t *init_ids, int icp) {
-    if (N < 1 || D < 1 || k < 1 || (int64_t)k > N || icp < 0 || icp > 2) return NULL;
+    if (N < 1 || D < 1 || k < 1 || (int64_t)k > N || icp < 0 || icp > 3) return NULL;
     orc *o = (orc *)xcalloc(1, sizeof(orc));
     if (!o) return NULL;
     o->N = N; o->D = D; o->k = k;
@@ -202,22 +209,39 @@ int orc_assign(orc *o, double *stats) {
             int32_t a_prev = o->prev_labels[i];
             /* Algorithm 4, line 6: branch once per object on lambda_{a(x_i)} */
             int filt = o->icp && a_prev >= 0 && o->own_ok[i] && o->lambda[a_prev] == 1;
-            for (int32_t j = 0; j < k; ++j) rho[j] = 0.0;
-            for (int64_t h = o->row_ptr[i]; h < o->row_ptr[i + 1]; ++h) {
-                int32_t s = o->idx[h];
-                double v = (double)o->val[h];
-                int64_t b = o->if_off[s];
-                if (filt && o->icp == 2) {
-                    /* Algorithm 3: every posting, a branch on lambda of its centroid */
-                    int64_t e = o->if_off[s + 1];
-                    for (int64_t q = b; q < e; ++q)
-                        if (o->lambda[o->if_cid[q]] == 0) rho[o->if_cid[q]] += v * o->if_u[q];
+            /* Relaxed filter (icp = 3): the own cluster moved, but the object
+             * keeps to the moving centroids if its similarity to its own
+             * centroid did not decrease; the own centroid is moving, so its new
+             * score comes out of the front scan. Otherwise everything is
+             * scanned again. It is tried only while at most half of the
+             * clusters are moving (a rejected try scans the fronts twice). */
+            int relax = o->icp == 3 && !filt && a_prev >= 0 && o->own_ok[i] && 2 * n_moving_prev <= k;
+            for (int pass = 0; pass < 2; ++pass) {
+                const int front = (filt || relax) && pass == 0;
+                for (int32_t j = 0; j < k; ++j) rho[j] = 0.0;
+                for (int64_t h = o->row_ptr[i]; h < o->row_ptr[i + 1]; ++h) {
+                    int32_t s = o->idx[h];
+                    double v = (double)o->val[h];
+                    int64_t b = o->if_off[s];
+                    if (filt && o->icp == 2) {
+                        /* Algorithm 3: every posting, a branch on lambda of its centroid */
+                        int64_t e = o->if_off[s + 1];
+                        for (int64_t q = b; q < e; ++q)
+                            if (o->lambda[o->if_cid[q]] == 0) rho[o->if_cid[q]] += v * o->if_u[q];
+                        postings += e - b;
+                        continue;
+                    }
+                    int64_t e = front ? b + o->if_mf0[s] : o->if_off[s + 1];
+                    for (int64_t q = b; q < e; ++q) rho[o->if_cid[q]] += v * o->if_u[q];
                     postings += e - b;
+                }
+                if (relax && pass == 0) {
+                    if (rho[a_prev] >= o->own[i]) break; /* accepted */
+                    simcalc += n_moving_prev;            /* the front scan was wasted */
+                    relax = 0;
                     continue;
                 }
-                int64_t e = filt ? b + o->if_mf0[s] : o->if_off[s + 1];
-                for (int64_t q = b; q < e; ++q) rho[o->if_cid[q]] += v * o->if_u[q];
-                postings += e - b;
+                break;
             }
             /* argmax: largest score, lowest index among equal scores */
             int32_t a = -1;
@@ -228,6 +252,9 @@ int orc_assign(orc *o, double *stats) {
                     if (j == a_prev) x = o->own[i];
                     else if (o->lambda[j] == 0) x = rho[j];
                     else continue; /* invariant centroid: not a candidate */
+                } else if (relax) {
+                    if (o->lambda[j] == 0) x = rho[j];
+                    else continue; /* the own centroid is among the moving ones */
                 } else {
                     x = rho[j];
                 }
@@ -244,9 +271,9 @@ int orc_assign(orc *o, double *stats) {
             o->second[i] = snd;
             o->own[i] = bst;
             o->own_ok[i] = 1;
-            o->filtered[i] = (uint8_t)filt;
-            simcalc += filt ? n_moving_prev : k;
-            nfilt += filt;
+            o->filtered[i] = (uint8_t)(filt || relax);
+            simcalc += (filt || relax) ? n_moving_prev : k;
+            nfilt += filt || relax;
         }
         free(rho);
     }

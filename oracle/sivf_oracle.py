@@ -107,7 +107,8 @@ class Oracle:
 
     def __init__(self, corpus, k: int, init_ids: np.ndarray, icp=True, threads: int = 0, lib=None):
         """icp: False/0 unfiltered (Algorithm 2), True/1 SIVF (Algorithm 4),
-        2 or "cbicp" IVF-CBICP (Algorithm 3)."""
+        2 or "cbicp" IVF-CBICP (Algorithm 3), 3 or "relaxed" SIVF with the
+        relaxed (own-similarity) filter."""
         self._lib = lib if lib is not None else _load()
         if threads:
             self._lib.orc_set_threads(int(threads))
@@ -118,7 +119,12 @@ class Oracle:
         init = np.ascontiguousarray(init_ids, dtype=np.int32)
         if init.shape != (self.k,):
             raise ValueError("init_ids must have k entries")
-        mode = 2 if (icp == "cbicp" or (not isinstance(icp, bool) and icp == 2)) else int(bool(icp))
+        if icp == "cbicp" or (not isinstance(icp, bool) and icp == 2):
+            mode = 2
+        elif icp == "relaxed" or (not isinstance(icp, bool) and icp == 3):
+            mode = 3
+        else:
+            mode = int(bool(icp))
         self._h = self._lib.orc_create(self.N, self.D, self.k, _p(self._row_ptr), _p(self._idx),
                                        _p(self._val), _p(init), mode)
         if not self._h:

@@ -376,7 +376,7 @@ sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t
     if (N < 1 || N > 0x7FFFFFFFll || D < 1 || D > (1 << 30) || k < 1 || (int64_t)k > N || !row_ptr || !idx || !val ||
         !init_ids)
         return SIVF_ERR_INVALID_ARG;
-    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16 || cfg->icp < 0 || cfg->icp > 2))
+    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16 || cfg->icp < 0 || cfg->icp > 3))
         return SIVF_ERR_INVALID_ARG;
     if (!distinct_ids(init_ids, k, N)) return SIVF_ERR_INVALID_ARG;
     if (cfg && cfg->inputs_on_host) {
@@ -419,7 +419,7 @@ sivf_status sivf_batch_init(sivf_ctx **out, const sivf_config *cfg, int32_t n_in
     if (!out) return SIVF_ERR_INVALID_ARG;
     *out = nullptr;
     if (n_inst < 1 || n_inst > 65536 || !descs) return SIVF_ERR_INVALID_ARG;
-    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16 || cfg->inputs_on_host || cfg->icp < 0 || cfg->icp > 2))
+    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16 || cfg->inputs_on_host || cfg->icp < 0 || cfg->icp > 3))
         return SIVF_ERR_INVALID_ARG;
     std::vector<int64_t> inst_obj(1, 0);
     std::vector<int32_t> inst_k(1, 0), inst_d(1, 0);

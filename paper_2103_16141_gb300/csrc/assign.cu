@@ -402,8 +402,12 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
         const uint32_t own_q = P.own[i];
         const bool filt = P.icp && a_prev >= 0 && own_q != OWN_INVALID && P.lam_prev[a_prev] != 0;
         const int mb = P.mov_beg[inst];
-        const int n_mov = filt ? P.mov_beg[inst + 1] - mb : 0;
+        const int n_mov_inst = P.mov_beg[inst + 1] - mb;
         const int32_t *movs = P.mov_list + mb;
+        // relaxed filter (icp = 3): the own cluster moved, and at most half of
+        // the instance's clusters are moving; decided after the front scan
+        bool relax = P.icp == 3 && !filt && a_prev >= 0 && own_q != OWN_INVALID && 2 * n_mov_inst <= km;
+        bool wasted = false;  // a relaxed front scan that was rejected
         // rho[id] += q; under CB a filtered object skips invariant centroids
         const bool cbf = CB && filt;
         auto add = [&](int id, float prod) {
@@ -429,6 +433,8 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
         //    short fronts keep every lane busy. Warp w takes a contiguous range
         //    of rows; each lane walks forward through the segments.
         constexpr int RMIN = 64;
+        for (int pass = 0;; ++pass) {
+        const bool front = (filt || relax) && pass == 0;  // scan the fronts only
         for (int64_t cb = rb; cb < re; cb += T) {
             const int cn = (int)min((int64_t)T, re - cb);
             int2 cnt = make_int2(0, 0);
@@ -436,7 +442,7 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
                 const int t = P.idx[cb + tid];
                 const int64_t o0 = P.if_off[t];
                 const int lfull = (int)(P.if_off[t + 1] - o0);
-                const int len = (filt && !CB) ? P.if_mf0[t] : lfull;
+                const int len = (front && !CB) ? P.if_mf0[t] : lfull;
                 const int fb = lfull & ~(SC_BLK - 1);
                 const int r0 = min(len, fb) & ~(SC_BLK - 1);  // postings in full, fully scanned blocks
                 const float vs = P.val[cb + tid] * FIX_SCALE;  // exact: power-of-two scaling
@@ -548,6 +554,27 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
             }
             __syncthreads();
         }
+        if (!relax) break;
+        // Relaxed test: keep to the moving centroids if the similarity to the
+        // own (moving) centroid did not decrease. Both scores are fixed-point
+        // approximations inside the error bound E, so the test asks for
+        // rho~_new - E(rho~_new) >= rho~_old + E(rho~_old), which implies it
+        // for the exact scores; otherwise scan everything again.
+        if (tid == 0) {
+            const double xn = (double)rho_ld<GRHO>(rho + a_loc) * FIX_QUANTUM;
+            const double xo = (double)own_q * FIX_QUANTUM;
+            const double S = (double)P.sumv[i];
+            s_flag = xn - error_bound(xn, re - rb, S, P.eps, P.eta) >= xo + error_bound(xo, re - rb, S, P.eps, P.eta);
+        }
+        __syncthreads();
+        if (s_flag) break;
+        for (int m = tid; m < n_mov_inst; m += T) rho_zero<GRHO>(rho + (movs[m] - k_off));
+        __syncthreads();
+        relax = false;
+        wasted = true;
+        }
+        const bool sub = filt || relax;  // candidates: the moving clusters (plus the carried own one if filt)
+        const int n_mov = sub ? n_mov_inst : 0;
 
         // ---- argmax over the candidates (Algorithm 4, lines 14-16) ----
         Top2 t;
@@ -555,7 +582,7 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
         t.bi = INT32_MAX;
         t.sv = -1;
         // candidates by local id (same order as global ids within the instance)
-        if (!filt) {
+        if (!sub) {
             for (int j = tid; j < km; j += T) top2_push(t, rho_ld<GRHO>(rho + j), j);
         } else {
             for (int m = tid; m < n_mov; m += T) {
@@ -595,12 +622,12 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
             double wbest = -1.0;
             int wj = INT32_MAX;
             int ncand = 0;
-            const int total = filt ? n_mov : km;
+            const int total = sub ? n_mov : km;
             for (int base = warp * 32; base < total; base += T) {
                 const int m = base + lane;
                 int j = -1;
                 if (m < total) {
-                    j = filt ? movs[m] - k_off : m;
+                    j = sub ? movs[m] - k_off : m;
                     if (rho_ld<GRHO>(rho + j) < thr) j = -1;
                 }
                 unsigned bal = __ballot_sync(0xffffffffu, j >= 0);
@@ -657,11 +684,12 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
                 if (a_prev >= 0) P.moving[a_prev] = 1;
                 if (P.n_inst > 1) atomicAdd(P.inst_changed + inst, 1ull);
             }
-            s_cnt[0] += filt ? 1ull : 0ull;
-            s_cnt[1] += filt ? (unsigned long long)n_mov : (unsigned long long)km;
+            s_cnt[0] += sub ? 1ull : 0ull;
+            s_cnt[1] += (sub ? (unsigned long long)n_mov : (unsigned long long)km) +
+                        (wasted ? (unsigned long long)n_mov_inst : 0ull);
         }
         __syncthreads();
-        if (!filt) {
+        if (!sub) {
             for (int j = tid; j < km; j += T) rho_zero<GRHO>(rho + j);
         } else {
             for (int m = tid; m < n_mov; m += T) rho_zero<GRHO>(rho + (movs[m] - k_off));

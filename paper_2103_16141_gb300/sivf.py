@@ -22,9 +22,12 @@ UPDATE_MODES = {"auto": 0, "dense": 1, "sort": 2}
 
 def icp_mode(icp) -> int:
     """False/0: unfiltered (Algorithm 2); True/1: SIVF (Algorithm 4);
-    2 or "cbicp": IVF-CBICP (Algorithm 3)."""
+    2 or "cbicp": IVF-CBICP (Algorithm 3); 3 or "relaxed": SIVF with the
+    relaxed (own-similarity) filter."""
     if icp == "cbicp" or (not isinstance(icp, bool) and icp == 2):
         return 2
+    if icp == "relaxed" or (not isinstance(icp, bool) and icp == 3):
+        return 3
     return int(bool(icp))
 
 

@@ -68,7 +68,12 @@ def lockstep(c, k, ini, iters, precision="fp32", icp=True, check_centroids=True,
                 assert st["changed"] == a.changed
                 assert st["n_moving"] == a.n_moving
                 assert np.array_equal(g.lam(), o.lam())
-                if icp:
+                if icp == "relaxed":
+                    # the GPU takes the relaxed test on error-bounded scores, so
+                    # it restricts a subset of the objects the oracle restricts
+                    assert st["filtered"] <= a.filtered
+                    assert st["postings"] >= a.postings
+                elif icp:
                     assert st["filtered"] == a.filtered
                     assert st["simcalc"] == a.simcalc
                     assert st["postings"] == a.postings

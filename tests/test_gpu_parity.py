@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from oracle import Oracle
-from synth import CONFIGS
+from synth import CONFIGS, generate, init_ids
 from synth.corpus import from_dense
 from tests.gpu_harness import (compare_centroids, compare_labels, corpus_for, gpu_instance, lockstep, rel,
                                OBJECTIVE_RTOL)
@@ -365,3 +365,29 @@ def test_cbicp_sivf_ivf_three_way_on_gpu():
     finally:
         for g in (s, v, b):
             g.close()
+
+
+@pytest.mark.parametrize("precision,case", [("fp32", (3000, 3000, 30, 31)), ("bf16", (2000, 1000, 25, 33)),
+                                            ("fp32", (4000, 2000, 20, 31))])
+def test_relaxed_filter_lockstep(precision, case):
+    """SIVF with the relaxed filter on the GPU: the oracle's labels at every
+    iteration, and the objects it restricts to the moving centroids are at
+    least SIVF's and at most the oracle's (its test is error-bounded)."""
+    N, D, k, seed = case
+    w = CONFIGS["c1"].scaled(N=N, D=D, k=k)
+    c = generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, seed)
+    ini = init_ids(w.N, w.k, seed)
+    recs = lockstep(c, k, ini, 60, precision=precision, icp="relaxed")
+    s = gpu_instance(c, k, ini, precision=precision)
+    try:
+        extra = 0
+        for r in recs:
+            s.assign()
+            extra += r["stats"]["filtered"] - s.stats()["filtered"]
+            assert r["stats"]["filtered"] >= s.stats()["filtered"]
+            if r["r"] > 1 and r["changed"] == 0:
+                break
+            s.update()
+        assert extra > 0
+    finally:
+        s.close()

@@ -20,14 +20,15 @@ MUTANTS = [
      "if (o->lambda[j] != 0) mf0[p] += 1; else mf1[p] += 1;",
      "int64_t *pos = (o->lambda[j] == 0) ? &q0[p] : &q1[p];",
      "int64_t *pos = (o->lambda[j] != 0) ? &q0[p] : &q1[p];"),
-    ("filtered_scan_truncated", "int64_t e = filt ? b + o->if_mf0[s] : o->if_off[s + 1];",
-     "int64_t e = filt ? b + o->if_mf0[s] / 2 : o->if_off[s + 1];"),
+    ("filtered_scan_truncated", "int64_t e = front ? b + o->if_mf0[s] : o->if_off[s + 1];",
+     "int64_t e = front ? b + o->if_mf0[s] / 2 : o->if_off[s + 1];"),
     ("no_unit_length", "nval[d] = w[p] / wn;", "nval[d] = w[p];"),
     ("posting_value_off_by_one", "for (int64_t q = b; q < e; ++q) rho[o->if_cid[q]] += v * o->if_u[q];",
      "for (int64_t q = b; q < e; ++q) rho[o->if_cid[q]] += v * o->if_u[q > b ? q - 1 : q];"),
     ("new_cluster_not_marked_moving", "                o->lambda[a1] = 0;\n", "\n"),
     ("update_objective_of_mean", "snorm[j] = sqrt(ss);", "snorm[j] = sqrt(ss) / (double)cnt;"),
     ("cbicp_branch_inverted", "if (o->lambda[o->if_cid[q]] == 0) rho", "if (o->lambda[o->if_cid[q]] == 1) rho"),
+    ("relaxed_test_inverted", "if (rho[a_prev] >= o->own[i]) break;", "if (rho[a_prev] < o->own[i]) break;"),
     ("unfiltered_when_invariant", "int filt = o->icp && a_prev >= 0 && o->own_ok[i] && o->lambda[a_prev] == 1;",
      "int filt = o->icp && a_prev >= 0 && o->own_ok[i] && o->lambda[a_prev] == 0;"),
 ]
@@ -45,6 +46,7 @@ def _battery(lib):
     pins.pin_monotone(21, lib)
     for s in (3, 4):
         pins.pin_cbicp(s, lib)
+    pins.pin_relaxed(0, lib)
 
 
 def _compile(src_text: str, out_dir: str, name: str):

@@ -321,6 +321,71 @@ def test_cbicp_filters_on_c1():
     assert filtered > 0
 
 
+RELAXED_CASES = [(3000, 3000, 30, 31), (2000, 1000, 25, 33), (4000, 2000, 20, 31)]
+
+
+@pytest.mark.parametrize("case", range(len(RELAXED_CASES)))
+def test_relaxed_filter_keeps_ivf_labels(case):
+    """The relaxed filter (an object whose own cluster moved keeps to the moving
+    centroids when its own similarity did not decrease) gives IVF's labels and
+    best scores at every iteration; it filters every object SIVF filters, and
+    each object it filters in addition has a best score no lower than at the
+    previous iteration."""
+    assert pin_relaxed(case) > 0
+
+
+def _own_similarity(c, lab, M, ids):
+    """FP64 <x_i, mu_lab(i)> summed term by term in row order (the scan's order)."""
+    out = np.empty(len(ids))
+    for n, i in enumerate(ids):
+        acc = 0.0
+        for h in range(c.row_ptr[i], c.row_ptr[i + 1]):
+            acc += float(c.val[h]) * M[lab[i], c.idx[h]]
+        out[n] = acc
+    return out
+
+
+def pin_relaxed(case, lib=None):
+    N, D, k, seed = RELAXED_CASES[case]
+    w = CONFIGS["c1"].scaled(N=N, D=D, k=k)
+    c = generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, seed)
+    ini = init_ids(w.N, w.k, seed)
+    f = Oracle(c, w.k, ini, icp=True, lib=lib)
+    g = Oracle(c, w.k, ini, icp=False, lib=lib)
+    h = Oracle(c, w.k, ini, icp="relaxed", lib=lib)
+    extra = 0
+    prev_best = None
+    for _ in range(40):
+        # the rule, from the paper's statement: an object of a moving cluster
+        # is restricted iff its similarity to its own centroid did not drop
+        lab_prev, lam_prev = h.labels(), h.lam()
+        eligible = np.zeros(w.N, dtype=bool)
+        if prev_best is not None and 2 * int((lam_prev == 0).sum()) <= w.k:
+            eligible = lam_prev[lab_prev] == 0
+        ids = np.nonzero(eligible)[0]
+        rise = _own_similarity(c, lab_prev, h.dense_centroids(), ids) >= prev_best[ids] if len(ids) else None
+        af, ag, ah = f.assign(), g.assign(), h.assign()
+        if len(ids):
+            assert np.array_equal(h.scores()[2][ids].astype(bool), rise)
+        assert np.array_equal(h.labels(), g.labels())
+        bh, _, fh = h.scores()
+        bg, _, _ = g.scores()
+        _, _, ff = f.scores()
+        assert np.array_equal(bh, bg)
+        assert np.all(fh >= ff)
+        more = (fh > ff)
+        if prev_best is not None:
+            assert np.all(bh[more] >= prev_best[more])
+        if 2 * ah.n_moving_prev > w.k:
+            assert ah.filtered == af.filtered and ah.postings == af.postings
+        extra += int(more.sum())
+        prev_best = bh
+        if ah.r > 1 and ah.changed == 0:
+            break
+        f.update(), g.update(), h.update()
+    return extra
+
+
 def test_icp_invariant_counts_and_monotone_objective_c1():
     w = CONFIGS["c1"]
     c = generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, w.seed)
