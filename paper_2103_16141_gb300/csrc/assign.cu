@@ -306,10 +306,12 @@ __device__ __forceinline__ void load_one(const AssignParams &P, int pos, int &id
 }
 
 // Register budget: resident CTAs per SM at 128 threads (scaled for other
-// block sizes). 10 caps a thread at 51 registers (measured best on the
-// 300K x 100K, k = 1000 corpus among 8, 10, 12 and 16).
+// block sizes). 12 caps a thread at 40 registers; on the 300K x 100K,
+// k = 1000 corpus it beat 10 (48 registers) and 8 (64) by 1-3 % (FP32) and
+// 3-9 % (BF16) per assignment, the extra resident warps outweighing the few
+// spilled values.
 #ifndef SIVF_ASSIGN_MIN_CTAS_128
-#define SIVF_ASSIGN_MIN_CTAS_128 10
+#define SIVF_ASSIGN_MIN_CTAS_128 12
 #endif
 // resident CTAs asked of the compiler for a block size (an SM holds at most 32)
 template <int T>
