@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
         //    to end and cut into rows of 32 postings, one posting per lane, so
         //    short fronts keep every lane busy. Warp w takes a contiguous range
         //    of rows; each lane walks forward through the segments.
-        constexpr int RMIN = 64;
+        constexpr int RMIN = 16;
         for (int pass = 0;; ++pass) {
         const bool front = (filt || relax) && pass == 0;  // scan the fronts only
         for (int64_t cb = rb; cb < re; cb += T) {
