@@ -410,6 +410,18 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
         // the instance's clusters are moving; decided after the front scan
         bool relax = P.icp == 3 && !filt && a_prev >= 0 && own_q != OWN_INVALID && 2 * n_mov_inst <= km;
         bool wasted = false;  // a relaxed front scan that was rejected
+        if (!CB && filt && n_mov_inst == 0) {
+            // an invariant cluster in an instance with no moving cluster (it
+            // has converged; only batches run on): the only candidate is the
+            // own cluster and every front is empty, so the label and the own
+            // score stay as they are
+            if (tid == 0) {
+                P.labels[i] = a_prev;
+                s_cnt[0] += 1;
+            }
+            __syncthreads();
+            continue;
+        }
         // rho[id] += q; under CB a filtered object skips invariant centroids
         const bool cbf = CB && filt;
         auto add = [&](int id, float prod) {
