@@ -646,38 +646,91 @@ __device__ __forceinline__ int64_t tiled_pos(int64_t p, int64_t L) {
     return (p & ~(int64_t)(SC_BLK - 1)) | ((p & 31) << 2) | ((p >> 5) & 3);
 }
 
-// Canonical arrays (if_cid: global cluster ids, if_val) in sorted order, and
-// the scan copy (local ids) at its tiled positions.
-__global__ void k_if_fill(const int64_t *n_dev, int64_t cap, const uint32_t *order, const uint32_t *skeys,
-                          const int64_t *if_off, const int64_t *sc_off, const int32_t *cclu, const int32_t *clu_koff,
-                          const float *cval, int prec, int32_t *if_cid, float *if_val, uint16_t *sc_id16,
-                          int32_t *sc_id32, float *sc_val, uint32_t *sc_pack, uint16_t *sc_lp) {
+// Canonical arrays (if_cid: global cluster ids, if_val) in sorted order.
+__global__ void k_if_fill(const int64_t *n_dev, int64_t cap, const uint32_t *order, const int32_t *cclu,
+                          const float *cval, int32_t *if_cid, float *if_val) {
     const int64_t n = min(*n_dev, cap);
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t e = order[q];
-        const float u = cval[e];
-        const int32_t j = cclu[e];
-        const uint32_t jl = (uint32_t)(j - clu_koff[j]);
-        if_cid[q] = j;
-        if_val[q] = u;
-        const uint32_t t = skeys[q] >> 1;
+        if_cid[q] = cclu[e];
+        if_val[q] = cval[e];
+    }
+}
+
+// Scan copy of the file, one warp per segment (the front or the back of a
+// list). Inside a segment the postings are reordered so that 32 consecutive
+// ones fall on distinct shared-memory banks of the score vector (bank =
+// local id mod 32) as far as the segment allows: by rank among the segment's
+// postings of the same bank, then by bank. Consecutive ranks then cover every
+// bank once while all banks last, and a window of 32 that straddles two such
+// ranks still does. The order inside a part does not change any score (each
+// posting is one integer add). The reordered postings are then stored at
+// their tiled positions with local ids and the scan's value encoding.
+constexpr int SC_COPY_THREADS = 256;
+__global__ void __launch_bounds__(SC_COPY_THREADS) k_if_scan_copy(
+    int32_t D, const int64_t *if_off, const int32_t *if_mf0, const int64_t *sc_off, const int32_t *if_cid,
+    const float *if_val, const int32_t *clu_koff, int prec, uint16_t *sc_id16, int32_t *sc_id32, float *sc_val,
+    uint32_t *sc_pack, uint16_t *sc_lp) {
+    __shared__ int s_cnt[SC_COPY_THREADS / 32][32];
+    __shared__ int s_run[SC_COPY_THREADS / 32][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    const int64_t nw = ((int64_t)gridDim.x * SC_COPY_THREADS) >> 5;
+    for (int64_t seg = (blockIdx.x * (int64_t)SC_COPY_THREADS + threadIdx.x) >> 5; seg < 2 * (int64_t)D; seg += nw) {
+        const int t = (int)(seg >> 1);
         const int64_t o = if_off[t];
-        const int64_t s = sc_off[t] + tiled_pos(q - o, if_off[t + 1] - o);
-        if (sc_id16) sc_id16[s] = (uint16_t)jl;
-        if (sc_id32) sc_id32[s] = (int32_t)jl;
-        if (prec == SIVF_FP32) {
-            sc_val[s] = u;
-            continue;
+        const int L = (int)(if_off[t + 1] - o), m0 = if_mf0[t];
+        const int s0 = (seg & 1) ? m0 : 0, n = (seg & 1) ? L - m0 : m0;
+        if (n <= 0) continue;
+        s_cnt[w][lane] = 0;
+        s_run[w][lane] = 0;
+        __syncwarp();
+        for (int c0 = 0; c0 < n; c0 += 32) {  // postings per bank
+            if (c0 + lane < n) {
+                const int32_t j = if_cid[o + s0 + c0 + lane];
+                atomicAdd(&s_cnt[w][(j - clu_koff[j]) & 31], 1);
+            }
         }
-        unsigned short lp;
-        if (prec == SIVF_BF16) {
-            lp = __bfloat16_as_ushort(__float2bfloat16_rn(u));
-        } else {
-            lp = __half_as_ushort(__float2half_rn(u * FP16_SCALE));
-            if (lp == 0 && u > 0.0f) lp = 1;  // keep every posting strictly positive
+        __syncwarp();
+        const int cnt = s_cnt[w][lane];  // lane b: postings of bank b
+        const int64_t base = sc_off[t];
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            const bool ok = c0 + lane < n;
+            const int64_t q = o + s0 + c0 + lane;
+            const int32_t j = ok ? if_cid[q] : 0;
+            const uint32_t jl = ok ? (uint32_t)(j - clu_koff[j]) : 0u;
+            const int bank = (int)(jl & 31);
+            const unsigned peers = __match_any_sync(0xffffffffu, ok ? bank : 32 + lane);
+            const int rank = (ok ? s_run[w][bank] : 0) + __popc(peers & below);
+            __syncwarp();
+            if (ok && (peers & below) == 0) s_run[w][bank] += __popc(peers);  // group leader
+            __syncwarp();
+            // destination in the segment: postings of lower rank, then lower banks of equal rank
+            int d = 0;
+#pragma unroll 8
+            for (int b = 0; b < 32; ++b) {
+                const int cb = __shfl_sync(0xffffffffu, cnt, b);
+                d += min(cb, rank) + ((b < bank && cb > rank) ? 1 : 0);
+            }
+            if (!ok) continue;
+            const int64_t pos = base + tiled_pos(s0 + d, L);  // s0 + d: index in the list
+            const float u = if_val[q];
+            if (sc_id16) sc_id16[pos] = (uint16_t)jl;
+            if (sc_id32) sc_id32[pos] = (int32_t)jl;
+            if (prec == SIVF_FP32) {
+                sc_val[pos] = u;
+                continue;
+            }
+            unsigned short lp;
+            if (prec == SIVF_BF16) {
+                lp = __bfloat16_as_ushort(__float2bfloat16_rn(u));
+            } else {
+                lp = __half_as_ushort(__float2half_rn(u * FP16_SCALE));
+                if (lp == 0 && u > 0.0f) lp = 1;  // keep every posting strictly positive
+            }
+            if (sc_pack) sc_pack[pos] = (jl << 16) | (uint32_t)lp;
+            else sc_lp[pos] = lp;
         }
-        if (sc_pack) sc_pack[s] = (jl << 16) | (uint32_t)lp;
-        else sc_lp[s] = lp;
     }
 }
 
@@ -794,11 +847,12 @@ cudaError_t build_inverted_file(sivf_ctx *c) {
     SIVF_CUDA_TRY(cudaMemcpyAsync(c->sc_off + c->D, total + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, c->stream));
     bool alt = false;
     SIVF_CUDA_TRY(radix_sort_pairs_dev(k0, v0, k1, v1, cap, n_dev, c->bits_t + 1, &alt, ws, c->stream));
-    k_if_fill<<<blocks_for(cap), TPB, 0, c->stream>>>(n_dev, cap, alt ? v1 : v0, alt ? k1 : k0, c->if_off, c->sc_off,
-                                                      c->cclu, c->clu_koff, c->cval[cur], (int)c->cfg.prec, c->if_cid,
-                                                      c->if_val, c->sc_id16, c->sc_id32, c->sc_val, c->sc_pack,
-                                                      c->sc_lp);
-    note_launch();
+    k_if_fill<<<blocks_for(cap), TPB, 0, c->stream>>>(n_dev, cap, alt ? v1 : v0, c->cclu, c->cval[cur], c->if_cid,
+                                                      c->if_val);
+    k_if_scan_copy<<<blocks_for((int64_t)2 * c->D * 32), SC_COPY_THREADS, 0, c->stream>>>(
+        c->D, c->if_off, c->if_mf0, c->sc_off, c->if_cid, c->if_val, c->clu_koff, (int)c->cfg.prec, c->sc_id16,
+        c->sc_id32, c->sc_val, c->sc_pack, c->sc_lp);
+    note_launch(2);
     SIVF_CUDA_TRY(cudaGetLastError());
     ws.used = mark;
     return cudaSuccess;
