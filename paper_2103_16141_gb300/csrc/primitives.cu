@@ -3,6 +3,9 @@
 //
 // Scan: reduce-then-scan in three launches (tile sums, one-CTA scan of the
 // tile sums, tile-local scan plus carry-in).
+// Every tile kernel loops over tiles with a grid of at most TILE_GRID blocks,
+// and when the element count is on the device it stops at the live tiles, so
+// a launch sized by a capacity costs no empty blocks.
 // Radix sort: digits of up to 10 bits (fewest passes for the key width), per
 // pass (1) per-tile digit histograms stored digit-major, (2) an exclusive
 // scan of that table, (3) a stable scatter whose in-tile ranks come from
@@ -22,6 +25,8 @@ int bits_for(uint64_t max_value) {
 namespace {
 
 constexpr int SCAN_THREADS = 256;
+constexpr int64_t TILE_GRID = 2048;
+inline unsigned tile_grid(int64_t tiles) { return (unsigned)(tiles < TILE_GRID ? (tiles > 0 ? tiles : 1) : TILE_GRID); }
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
@@ -60,19 +65,27 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_tile_sums(const T *in, int6
     __shared__ T warp_s[32];
     __shared__ T total;
     if (n_dev) n = min(*n_dev, n);  // never past the launch bound
-    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
-    T s = 0;
+    const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {  // block-uniform
+        const int64_t base = t * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+        T s = 0;
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i)
-        if (base + i < n) s += in[base + i];
-    block_exclusive_scan<T>(s, warp_s, &total);
-    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+        for (int i = 0; i < SCAN_ITEMS; ++i)
+            if (base + i < n) s += in[base + i];
+        block_exclusive_scan<T>(s, warp_s, &total);
+        if (threadIdx.x == 0) tile_sums[t] = total;
+        __syncthreads();
+    }
 }
 
+// n: tile sums, or the tile count of the element bound when n_dev (element
+// count on the device) is given; only the live tiles are scanned.
 template <typename T>
-__global__ void __launch_bounds__(1024) scan_single_block(T *data, int64_t n, T *total_out) {
+__global__ void __launch_bounds__(1024) scan_single_block(T *data, int64_t n, const int64_t *n_dev, int64_t nmax,
+                                                          T *total_out) {
     __shared__ T warp_s[32];
     __shared__ T total;
+    if (n_dev) n = (min(*n_dev, nmax) + SCAN_TILE - 1) / SCAN_TILE;
     T carry = 0;
     for (int64_t b = 0; b < n; b += blockDim.x) {
         int64_t i = b + threadIdx.x;
@@ -91,19 +104,23 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_tiles(const T *in, T *out, 
     __shared__ T warp_s[32];
     __shared__ T total;
     if (n_dev) n = min(*n_dev, n);  // never past the launch bound
-    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
-    T v[SCAN_ITEMS];
-    T s = 0;
+    const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {  // block-uniform
+        const int64_t base = t * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+        T v[SCAN_ITEMS];
+        T s = 0;
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i) {
-        v[i] = base + i < n ? in[base + i] : T(0);
-        s += v[i];
-    }
-    T ex = block_exclusive_scan<T>(s, warp_s, &total) + tile_offs[blockIdx.x];
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            v[i] = base + i < n ? in[base + i] : T(0);
+            s += v[i];
+        }
+        T ex = block_exclusive_scan<T>(s, warp_s, &total) + tile_offs[t];
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i) {
-        if (base + i < n) out[base + i] = ex;
-        ex += v[i];
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            if (base + i < n) out[base + i] = ex;
+            ex += v[i];
+        }
+        __syncthreads();
     }
 }
 
@@ -119,9 +136,9 @@ cudaError_t scan_exclusive_impl(const T *in, T *out, int64_t n, T *total, Worksp
     size_t mark = ws.used;
     T *sums = ws.take<T>((size_t)tiles);
     if (!sums) return cudaErrorMemoryAllocation;
-    scan_tile_sums<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, n_dev, sums);
-    scan_single_block<T><<<1, 1024, 0, s>>>(sums, tiles, total);
-    scan_tiles<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, n_dev, sums);
+    scan_tile_sums<T><<<tile_grid(tiles), SCAN_THREADS, 0, s>>>(in, n, n_dev, sums);
+    scan_single_block<T><<<1, 1024, 0, s>>>(sums, tiles, n_dev, n, total);
+    scan_tiles<T><<<tile_grid(tiles), SCAN_THREADS, 0, s>>>(in, out, n, n_dev, sums);
     note_launch(3);
     ws.used = mark;
     return cudaGetLastError();
@@ -146,16 +163,18 @@ __global__ void __launch_bounds__(RS_THREADS) radix_hist(const uint32_t *keys, i
     if (n_dev) n = min(*n_dev, n);  // never past the launch bound
     const int64_t live = (n + RS_TILE - 1) / RS_TILE;
     if (blockIdx.x == 0 && threadIdx.x == 0) *scan_n = live * R;
-    if ((int64_t)blockIdx.x >= live) return;  // block-uniform
-    for (int d = threadIdx.x; d < R; d += RS_THREADS) h[d] = 0;
-    __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
-        int64_t p = base + i;
-        if (p < n) atomicAdd(&h[(keys[p] >> shift) & mask], 1u);
+    for (int64_t t = blockIdx.x; t < live; t += gridDim.x) {  // block-uniform
+        for (int d = threadIdx.x; d < R; d += RS_THREADS) h[d] = 0;
+        __syncthreads();
+        const int64_t base = t * RS_TILE;
+        for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
+            const int64_t p = base + i;
+            if (p < n) atomicAdd(&h[(keys[p] >> shift) & mask], 1u);
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < R; d += RS_THREADS) counts[(int64_t)d * live + t] = h[d];
+        __syncthreads();
     }
-    __syncthreads();
-    for (int d = threadIdx.x; d < R; d += RS_THREADS) counts[(int64_t)d * live + blockIdx.x] = h[d];
 }
 
 template <int BITS>
@@ -169,53 +188,55 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter(const uint32_t *__re
     __shared__ uint32_t wcnt[RS_WARPS][R];
     __shared__ uint32_t toff[R];
     if (n_dev) n = min(*n_dev, n);  // never past the launch bound
-    if ((int64_t)blockIdx.x * RS_TILE >= n) return;  // tile past the live count (block-uniform)
     const int64_t live = (n + RS_TILE - 1) / RS_TILE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < R; d += RS_THREADS) {
+    for (int64_t t = blockIdx.x; t < live; t += gridDim.x) {  // block-uniform
+        for (int d = threadIdx.x; d < R; d += RS_THREADS) {
 #pragma unroll
-        for (int w = 0; w < RS_WARPS; ++w) wcnt[w][d] = 0;
-        toff[d] = offs[(int64_t)d * live + blockIdx.x];
-    }
-    __syncthreads();
-    const int64_t wbase = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * (32 * RS_ITEMS);
-    uint32_t kk[RS_ITEMS], vv[RS_ITEMS], rk[RS_ITEMS];
-    const unsigned lt = (1u << lane) - 1u;
-#pragma unroll
-    for (int r = 0; r < RS_ITEMS; ++r) {
-        int64_t p = wbase + r * 32 + lane;
-        bool valid = p < n;
-        uint32_t key = valid ? kin[p] : 0u;
-        kk[r] = key;
-        vv[r] = valid ? vin[p] : 0u;
-        uint32_t d = valid ? ((key >> shift) & mask) : (uint32_t)R;  // sentinel groups invalid lanes
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        uint32_t old = valid ? wcnt[warp][d] : 0u;
-        __syncwarp();
-        if (valid && (peers & lt) == 0) wcnt[warp][d] = old + (uint32_t)__popc(peers);
-        __syncwarp();
-        rk[r] = old + (uint32_t)__popc(peers & lt);
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < R; d += RS_THREADS) {
-        uint32_t run = 0;
-#pragma unroll
-        for (int w = 0; w < RS_WARPS; ++w) {
-            uint32_t c = wcnt[w][d];
-            wcnt[w][d] = run;
-            run += c;
+            for (int w = 0; w < RS_WARPS; ++w) wcnt[w][d] = 0;
+            toff[d] = offs[(int64_t)d * live + t];
         }
-    }
-    __syncthreads();
+        __syncthreads();
+        const int64_t wbase = t * RS_TILE + (int64_t)warp * (32 * RS_ITEMS);
+        uint32_t kk[RS_ITEMS], vv[RS_ITEMS], rk[RS_ITEMS];
+        const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-    for (int r = 0; r < RS_ITEMS; ++r) {
-        int64_t p = wbase + r * 32 + lane;
-        if (p < n) {
-            uint32_t d = (kk[r] >> shift) & mask;
-            uint32_t pos = toff[d] + wcnt[warp][d] + rk[r];
-            kout[pos] = kk[r];
-            vout[pos] = vv[r];
+        for (int r = 0; r < RS_ITEMS; ++r) {
+            int64_t p = wbase + r * 32 + lane;
+            bool valid = p < n;
+            uint32_t key = valid ? kin[p] : 0u;
+            kk[r] = key;
+            vv[r] = valid ? vin[p] : 0u;
+            uint32_t d = valid ? ((key >> shift) & mask) : (uint32_t)R;  // sentinel groups invalid lanes
+            unsigned peers = __match_any_sync(0xffffffffu, d);
+            uint32_t old = valid ? wcnt[warp][d] : 0u;
+            __syncwarp();
+            if (valid && (peers & lt) == 0) wcnt[warp][d] = old + (uint32_t)__popc(peers);
+            __syncwarp();
+            rk[r] = old + (uint32_t)__popc(peers & lt);
         }
+        __syncthreads();
+        for (int d = threadIdx.x; d < R; d += RS_THREADS) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < RS_WARPS; ++w) {
+                uint32_t c = wcnt[w][d];
+                wcnt[w][d] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < RS_ITEMS; ++r) {
+            int64_t p = wbase + r * 32 + lane;
+            if (p < n) {
+                uint32_t d = (kk[r] >> shift) & mask;
+                uint32_t pos = toff[d] + wcnt[warp][d] + rk[r];
+                kout[pos] = kk[r];
+                vout[pos] = vv[r];
+            }
+        }
+        __syncthreads();  // wcnt and toff are rewritten for the next tile
     }
 }
 
@@ -223,13 +244,13 @@ template <int BITS>
 void radix_pass(const uint32_t *ka, const uint32_t *va, uint32_t *kb, uint32_t *vb, int64_t n, const int64_t *n_dev,
                 int shift, uint32_t *counts, int64_t *scan_n, int64_t tiles, Workspace &ws, cudaStream_t s,
                 cudaError_t *err) {
-    radix_hist<BITS><<<(unsigned)tiles, RS_THREADS, 0, s>>>(ka, n, n_dev, shift, counts, scan_n);
+    radix_hist<BITS><<<tile_grid(tiles), RS_THREADS, 0, s>>>(ka, n, n_dev, shift, counts, scan_n);
     cudaError_t e = scan_exclusive_impl<uint32_t>(counts, counts, tiles * (1 << BITS), nullptr, ws, s, scan_n);
     if (e != cudaSuccess) {
         *err = e;
         return;
     }
-    radix_scatter<BITS><<<(unsigned)tiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, n_dev, shift, counts, tiles);
+    radix_scatter<BITS><<<tile_grid(tiles), RS_THREADS, 0, s>>>(ka, va, kb, vb, n, n_dev, shift, counts, tiles);
     note_launch(2);
 }
 

@@ -35,6 +35,15 @@ inline unsigned blocks_for(int64_t n, int tpb = TPB) {
     return (unsigned)b;
 }
 
+// Grid of a grid-stride kernel: enough blocks to fill the GPU a few times
+// over, not one per element, so that a launch bounded by a capacity (with the
+// live count on the device) costs no empty blocks.
+constexpr unsigned GS_MAX_BLOCKS = 4096;
+inline unsigned blocks_gs(int64_t n, int tpb = TPB) {
+    const unsigned b = blocks_for(n, tpb);
+    return b < GS_MAX_BLOCKS ? b : GS_MAX_BLOCKS;
+}
+
 // ---------------- validation and set-up ----------------
 
 // bad bits: 1 row_ptr, 2 idx range/order, 4 value, 8 norm
@@ -740,7 +749,7 @@ cudaError_t validate_csr(sivf_ctx *c, int *bad_host) {
     int *bad = c->ws.take<int>(1);
     if (!bad) return cudaErrorMemoryAllocation;
     SIVF_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
-    k_validate<<<blocks_for(c->N * 32), TPB, 0, c->stream>>>(c->N, c->D, c->nnz, c->row_ptr, c->idx, c->val,
+    k_validate<<<blocks_gs(c->N * 32), TPB, 0, c->stream>>>(c->N, c->D, c->nnz, c->row_ptr, c->idx, c->val,
                                                                c->sumv, bad);
     note_launch();
     SIVF_CUDA_TRY(cudaGetLastError());
@@ -780,14 +789,14 @@ cudaError_t set_labels_dev(sivf_ctx *c, const int32_t *src) {
     int *bad = c->ws.take<int>(1);
     if (!bad) return cudaErrorMemoryAllocation;
     SIVF_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
-    k_check_labels<<<blocks_for(c->N), TPB, 0, c->stream>>>(c->N, c->k, src, bad);
+    k_check_labels<<<blocks_gs(c->N), TPB, 0, c->stream>>>(c->N, c->k, src, bad);
     note_launch();
     int bad_h = 0;
     SIVF_CUDA_TRY(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     SIVF_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (bad_h) return cudaErrorInvalidValue;
     SIVF_CUDA_TRY(cudaMemsetAsync(c->moving, 0, c->k, c->stream));
-    k_set_labels<<<blocks_for(c->N), TPB, 0, c->stream>>>(c->N, src, c->labels, c->labels_prev, c->own, c->moving);
+    k_set_labels<<<blocks_gs(c->N), TPB, 0, c->stream>>>(c->N, src, c->labels, c->labels_prev, c->own, c->moving);
     note_launch();
     SIVF_CUDA_TRY(cudaGetLastError());
     if (c->iter == 0) c->iter = 1;  // first membership: every cluster is moving
@@ -836,7 +845,7 @@ cudaError_t build_inverted_file(sivf_ctx *c) {
     uint32_t *k1 = ws.take<uint32_t>((size_t)cap + 1), *v1 = ws.take<uint32_t>((size_t)cap + 1);
     if (!cnt2 || !len || !slen || !total || !k0 || !v0 || !k1 || !v1) return cudaErrorMemoryAllocation;
     SIVF_CUDA_TRY(cudaMemsetAsync(cnt2, 0, sizeof(uint32_t) * 2 * c->D, c->stream));
-    k_if_keys<<<blocks_for(cap), TPB, 0, c->stream>>>(n_dev, cap, c->cterm[cur], c->cclu, c->lam,
+    k_if_keys<<<blocks_gs(cap), TPB, 0, c->stream>>>(n_dev, cap, c->cterm[cur], c->cclu, c->lam,
                                                       c->cfg.icp == 2 ? 0 : 1, k0, v0, cnt2);
     k_if_lens<<<blocks_for(c->D), TPB, 0, c->stream>>>(c->D, cnt2, len, slen, c->if_mf0);
     note_launch(2);
@@ -847,9 +856,9 @@ cudaError_t build_inverted_file(sivf_ctx *c) {
     SIVF_CUDA_TRY(cudaMemcpyAsync(c->sc_off + c->D, total + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, c->stream));
     bool alt = false;
     SIVF_CUDA_TRY(radix_sort_pairs_dev(k0, v0, k1, v1, cap, n_dev, c->bits_t + 1, &alt, ws, c->stream));
-    k_if_fill<<<blocks_for(cap), TPB, 0, c->stream>>>(n_dev, cap, alt ? v1 : v0, c->cclu, c->cval[cur], c->if_cid,
+    k_if_fill<<<blocks_gs(cap), TPB, 0, c->stream>>>(n_dev, cap, alt ? v1 : v0, c->cclu, c->cval[cur], c->if_cid,
                                                       c->if_val);
-    k_if_scan_copy<<<blocks_for((int64_t)2 * c->D * 32), SC_COPY_THREADS, 0, c->stream>>>(
+    k_if_scan_copy<<<blocks_gs((int64_t)2 * c->D * 32, SC_COPY_THREADS), SC_COPY_THREADS, 0, c->stream>>>(
         c->D, c->if_off, c->if_mf0, c->sc_off, c->if_cid, c->if_val, c->clu_koff, (int)c->cfg.prec, c->sc_id16,
         c->sc_id32, c->sc_val, c->sc_pack, c->sc_lp);
     note_launch(2);
@@ -873,11 +882,11 @@ cudaError_t run_update_dense(sivf_ctx *c) {
     if (!cnt || !flag || !sz || !newn_d || !moved_d || !jAd || !jUd) return cudaErrorMemoryAllocation;
     SIVF_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * k, s));
     SIVF_CUDA_TRY(cudaMemsetAsync(moved_d, 0, sizeof(int64_t), s));
-    k_label_counts<<<blocks_for(N), TPB, 0, s>>>(N, c->labels, cnt);
+    k_label_counts<<<blocks_gs(N), TPB, 0, s>>>(N, c->labels, cnt);
     k_recompute_flags<<<blocks_for(k), TPB, 0, s>>>(k, c->lam, cnt, flag);
     const float fscale = ldexpf(1.0f, c->acc_shift);
     const double inv_scale = ldexp(1.0, -c->acc_shift);
-    k_acc_scatter<<<blocks_for(N * 32), TPB, 0, s>>>(N, c->labels, c->acc_lab, c->row_ptr, c->idx, c->val,
+    k_acc_scatter<<<blocks_gs(N * 32), TPB, 0, s>>>(N, c->labels, c->acc_lab, c->row_ptr, c->idx, c->val,
                                                      c->clu_doff, c->acc_off, fscale, c->acc, moved_d);
     k_acc_rows1<<<(unsigned)k, WR_THREADS, 0, s>>>(k, flag, cnt, c->acc_off, c->clu_doff, c->acc, inv_scale,
                                                    c->coff[cur], c->cterm[cur], c->cval[cur], c->snorm, sz,
@@ -890,7 +899,7 @@ cudaError_t run_update_dense(sivf_ctx *c) {
                                                    c->cterm[cur], c->cval[cur], c->snorm_new, c->coff[nw],
                                                    c->cterm[nw], c->cval[nw], c->cclu, c->cap_c, &c->ctr->error);
     k_sum_inst<<<(unsigned)c->n_inst, 1024, 0, s>>>(c->inst_k, jAd, jUd, c->obj_dev);
-    k_copy_back<<<blocks_for(c->cap_c), TPB, 0, s>>>(k, c->cap_c, c->coff[nw], c->cterm[nw], c->cval[nw],
+    k_copy_back<<<blocks_gs(c->cap_c), TPB, 0, s>>>(k, c->cap_c, c->coff[nw], c->cterm[nw], c->cval[nw],
                                                      c->snorm_new, c->coff[cur], c->cterm[cur], c->cval[cur],
                                                      c->snorm);
     note_launch(3);
@@ -930,7 +939,7 @@ cudaError_t run_update(sivf_ctx *c) {
         !jAd || !jUd || !tc || !toff || !ubeg || !uend)
         return cudaErrorMemoryAllocation;
     SIVF_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * k, s));
-    k_label_keys<<<blocks_for(N), TPB, 0, s>>>(N, c->labels, lk0, lv0, cnt);
+    k_label_keys<<<blocks_gs(N), TPB, 0, s>>>(N, c->labels, lk0, lv0, cnt);
     note_launch();
     bool alt = false;
     SIVF_CUDA_TRY(radix_sort_pairs(lk0, lv0, lk1, lv1, N, bits_for((uint64_t)(k - 1)), &alt, ws, s));
@@ -942,7 +951,7 @@ cudaError_t run_update(sivf_ctx *c) {
     // u2: tuples of the recomputed clusters' members, in member order; a
     // stable sort by term then a stable sort by cluster rank leave them in
     // (rank, term, object) order; equal (rank, term) runs are summed in FP64
-    k_member_tuples<<<blocks_for(N), TPB, 0, s>>>(N, perm, c->labels, flag, c->row_ptr, tc);
+    k_member_tuples<<<blocks_gs(N), TPB, 0, s>>>(N, perm, c->labels, flag, c->row_ptr, tc);
     note_launch();
     SIVF_CUDA_TRY(scan_exclusive_i64(tc, toff, N, T_d, ws, s));
     uint32_t *sa_k = ws.take<uint32_t>(Tmax), *sa_v = ws.take<uint32_t>(Tmax);
@@ -960,17 +969,17 @@ cudaError_t run_update(sivf_ctx *c) {
         // one sort on (rank, local term) carrying the value bits
         int32_t *rank2clu = reinterpret_cast<int32_t *>(tterm);
         k_rank2clu<<<blocks_for(k), TPB, 0, s>>>(k, flag, rrank, rank2clu);
-        k_expand_packed<<<blocks_for(N * 32), TPB, 0, s>>>(N, perm, c->labels, rrank, tc, toff, c->row_ptr, c->idx,
+        k_expand_packed<<<blocks_gs(N * 32), TPB, 0, s>>>(N, perm, c->labels, rrank, tc, toff, c->row_ptr, c->idx,
                                                             c->val, c->clu_doff, c->bits_tl, sa_k, sa_v);
         note_launch(2);
         bool a1 = false;
         SIVF_CUDA_TRY(radix_sort_pairs_dev(sa_k, sa_v, sb_k, sb_v, Tmax, T_d, bits_r + c->bits_tl, &a1, ws, s));
-        k_unpack<<<blocks_for(Tmax), TPB, 0, s>>>(Tmax, T_d, a1 ? sb_k : sa_k, a1 ? sb_v : sa_v, c->bits_tl, rank2clu,
+        k_unpack<<<blocks_gs(Tmax), TPB, 0, s>>>(Tmax, T_d, a1 ? sb_k : sa_k, a1 ? sb_v : sa_v, c->bits_tl, rank2clu,
                                                   c->clu_doff, key64, sval);
         note_launch();
     } else {
         // two stable sorts: by global term, then by rank
-        k_expand<<<blocks_for(N * 32), TPB, 0, s>>>(N, perm, c->labels, rrank, tc, toff, c->row_ptr, c->idx, c->val,
+        k_expand<<<blocks_gs(N * 32), TPB, 0, s>>>(N, perm, c->labels, rrank, tc, toff, c->row_ptr, c->idx, c->val,
                                                      sa_k, sa_v, tterm, tval, trank);
         note_launch();
         bool a1 = false;
@@ -978,24 +987,24 @@ cudaError_t run_update(sivf_ctx *c) {
         uint32_t *x_v = a1 ? sb_v : sa_v;                           // tuple ids sorted by term
         uint32_t *y_k = a1 ? sa_k : sb_k, *y_v = a1 ? sa_v : sb_v;  // the free pair
         uint32_t *z_k = a1 ? sb_k : sa_k;                           // its ping-pong partner
-        k_rank_keys<<<blocks_for(Tmax), TPB, 0, s>>>(Tmax, T_d, x_v, trank, y_k, y_v);
+        k_rank_keys<<<blocks_gs(Tmax), TPB, 0, s>>>(Tmax, T_d, x_v, trank, y_k, y_v);
         note_launch();
         bool a2 = false;
         SIVF_CUDA_TRY(radix_sort_pairs_dev(y_k, y_v, z_k, x_v, Tmax, T_d, bits_r, &a2, ws, s));
         const uint32_t *r_k = a2 ? z_k : y_k, *r_v = a2 ? x_v : y_v;
-        k_compose<<<blocks_for(Tmax), TPB, 0, s>>>(Tmax, T_d, r_k, r_v, tterm, tval, key64, sval);
+        k_compose<<<blocks_gs(Tmax), TPB, 0, s>>>(Tmax, T_d, r_k, r_v, tterm, tval, key64, sval);
         note_launch();
     }
     // the sort buffers are free again: run flags, run index, run position
     uint32_t *head = sa_k, *uidx = sa_v, *hpos = sb_k;
-    k_heads<<<blocks_for(Tmax), TPB, 0, s>>>(Tmax, T_d, key64, head);
+    k_heads<<<blocks_gs(Tmax), TPB, 0, s>>>(Tmax, T_d, key64, head);
     note_launch();
     SIVF_CUDA_TRY(scan_exclusive_u32_dev(head, uidx, Tmax, T_d, U_d, ws, s));
     SIVF_CUDA_TRY(cudaMemsetAsync(ubeg, 0, sizeof(int64_t) * (k + 1), s));  // empty-row clusters: no entries
     SIVF_CUDA_TRY(cudaMemsetAsync(uend, 0, sizeof(int64_t) * (k + 1), s));
-    k_head_pos<<<blocks_for(Tmax), TPB, 0, s>>>(Tmax, T_d, head, uidx, hpos);
-    k_seg_pieces<<<blocks_for((Tmax + 31) / 32 * 32), TPB, 0, s>>>(Tmax, T_d, key64, sval, part);
-    k_seg_runs<<<blocks_for(Tmax), TPB, 0, s>>>(Tmax, T_d, U_d, key64, hpos, part, uterm, usum, ubeg, uend);
+    k_head_pos<<<blocks_gs(Tmax), TPB, 0, s>>>(Tmax, T_d, head, uidx, hpos);
+    k_seg_pieces<<<blocks_gs((Tmax + 31) / 32 * 32), TPB, 0, s>>>(Tmax, T_d, key64, sval, part);
+    k_seg_runs<<<blocks_gs(Tmax), TPB, 0, s>>>(Tmax, T_d, U_d, key64, hpos, part, uterm, usum, ubeg, uend);
     note_launch(3);
     SIVF_CUDA_TRY(cudaGetLastError());
 
@@ -1008,7 +1017,7 @@ cudaError_t run_update(sivf_ctx *c) {
         k, flag, rrank, ubeg, uend, uterm, usum, cnt, c->coff[cur], c->cterm[cur], c->cval[cur], c->snorm,
         c->coff[nw], c->cterm[nw], c->cval[nw], c->cclu, c->snorm_new, jAd, jUd, c->cap_c, &c->ctr->error);
     k_sum_inst<<<(unsigned)c->n_inst, 1024, 0, s>>>(c->inst_k, jAd, jUd, c->obj_dev);
-    k_copy_back<<<blocks_for(c->cap_c), TPB, 0, s>>>(k, c->cap_c, c->coff[nw], c->cterm[nw], c->cval[nw],
+    k_copy_back<<<blocks_gs(c->cap_c), TPB, 0, s>>>(k, c->cap_c, c->coff[nw], c->cterm[nw], c->cval[nw],
                                                      c->snorm_new, c->coff[cur], c->cterm[cur], c->cval[cur],
                                                      c->snorm);
     note_launch(3);
