@@ -162,27 +162,38 @@ def barrier_and_sync(world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    torch.cuda.synchronize()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
+
+
+def _reduce(x, world, op):
+    """All-reduce of one host scalar over the ranks (device tensor under NCCL,
+    host tensor under gloo)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
+    return float(t.item())
 
 
 def max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return _reduce(x, world, dist.ReduceOp.MAX) if world > 1 else x
 
 
 def sum_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, world, dist.ReduceOp.SUM) if world > 1 else x
+
+
+def replica_throughput(units_local, ms_local, world):
+    """Whole-job throughput of independent replicas: the units every rank
+    processed over the slowest rank's time (ms). Returns (units/s, max ms)."""
+    ms = max_over_ranks(ms_local, world)
+    return sum_over_ranks(float(units_local), world) / (ms / 1e3), ms
 
 
 def cpu_baseline(w, c, ini, iters, icp=1):
@@ -283,8 +294,7 @@ def run_batched(args):
     ev1.record(stream)
     barrier_and_sync(world)
     clocks = sampler.stop()
-    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
-    value = sum_over_ranks(float(obj_iters), world) / (ms / 1e3)
+    value, ms = replica_throughput(obj_iters, ev0.elapsed_time(ev1), world)
     if rank == 0:
         nnz = sum(c.nnz for c in cs)
         line = {"metric": "objects/s (Lloyd iterations of SIVF spherical k-means, 64 batched instances)",
@@ -370,11 +380,8 @@ def main():
     ev1.record(stream)
     barrier_and_sync(world)
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    ms = max_over_ranks(ms, world)
     launches = sum(p["launches_run"] for p in all_per if "launches_run" in p)
-    objects = sum_over_ranks(float(w.N * tot_iters), world)
-    value = objects / (ms / 1e3)
+    value, ms = replica_throughput(w.N * tot_iters, ev0.elapsed_time(ev1), world)
 
     # roofline of the dominant kernel (the assignment scan), from the library's
     # per-launch event timings: over the timed region when steps are launched
