@@ -72,7 +72,7 @@ sivf_status check_usable(sivf_ctx *c) {
 void pick_assign_config(sivf_ctx *c) {
     int T = c->cfg.threads;
     if (T != 32 && T != 64 && T != 128 && T != 256 && T != 512) T = 0;
-    if (T == 0) T = c->kmax <= 256 ? 64 : (c->kmax <= 4096 ? 128 : 512);
+    if (T == 0) T = c->kmax <= 2048 ? 64 : (c->kmax <= 4096 ? 128 : 512);  // measured on the k = 1000 and k = 10,000 corpora
     c->assign_threads = T;
     c->assign_ctas_per_sm = c->cfg.ctas_per_sm > 0 ? c->cfg.ctas_per_sm : 0;
     int dev = 0, smem = 0;
