@@ -400,9 +400,7 @@ __global__ void __launch_bounds__(WR_THREADS) k_write_rows(
     }
 }
 
-// Per-instance objective sums (one CTA per instance), fixed order:
-// per-thread strided partial sums, then a tree.
-// copy the new rows back over the current ones (fixed buffers for graph replay)
+// Copy the new rows back over the current ones (fixed buffers for graph replay).
 __global__ void k_copy_back(int32_t k, int64_t cap, const int64_t *coff_src, const int32_t *term_src,
                             const float *val_src, const double *sn_src, int64_t *coff_dst, int32_t *term_dst,
                             float *val_dst, double *sn_dst) {
@@ -416,6 +414,8 @@ __global__ void k_copy_back(int32_t k, int64_t cap, const int64_t *coff_src, con
     for (int64_t j = g; j < k; j += st) sn_dst[j] = sn_src[j];
 }
 
+// Per-instance objective sums (one CTA per instance), fixed order:
+// per-thread strided partial sums, then a tree.
 __global__ void __launch_bounds__(1024) k_sum_inst(const int32_t *inst_k, const double *a, const double *b,
                                                    double *out) {
     __shared__ double sa[1024], sb[1024];
