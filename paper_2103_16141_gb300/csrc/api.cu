@@ -248,12 +248,13 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
     INIT_CUDA(dmalloc(c, &c->objf_dev, ni), "alloc");
     {
         // dense update accumulator: one row of the instance's D terms per cluster
+        // (padded to an even length; the pad entry stays zero)
         std::vector<int64_t> aoff((size_t)k + 1, 0);
         int64_t nmax = 1;
         for (int32_t m = 0; m < ni; ++m) {
             nmax = std::max(nmax, inst_obj[(size_t)m + 1] - inst_obj[(size_t)m]);
             for (int32_t j = inst_k[(size_t)m]; j < inst_k[(size_t)m + 1]; ++j)
-                aoff[(size_t)j + 1] = aoff[(size_t)j] + (inst_d[(size_t)m + 1] - inst_d[(size_t)m]);
+                aoff[(size_t)j + 1] = aoff[(size_t)j] + ((inst_d[(size_t)m + 1] - inst_d[(size_t)m] + 1) & ~1);  // rows 16-byte aligned
         }
         const size_t acc_bytes = 8 * (size_t)aoff[(size_t)k];
         bool dense = c->cfg.update_mode == 1;

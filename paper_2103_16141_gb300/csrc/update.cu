@@ -524,13 +524,24 @@ __global__ void __launch_bounds__(WR_THREADS) k_acc_rows1(
     const int64_t base = acc_off[j], L = acc_off[j + 1] - base;
     long long nz = 0;
     double ss = 0.0;
-    for (int64_t t = threadIdx.x; t < L; t += WR_THREADS) {
-        const long long v = acc[base + t];
+    // rows start at even entries and have even lengths: 16-byte loads, two
+    // of them in flight per thread
+    const longlong2 *row = reinterpret_cast<const longlong2 *>(acc + base);
+    const int64_t L2 = L >> 1;
+    auto take = [&](long long v) {
         if (v) {
             ++nz;
             const double x = (double)v * inv_scale;
             ss += x * x;
         }
+    };
+    for (int64_t p = threadIdx.x; p < L2; p += 2 * WR_THREADS) {
+        const longlong2 a = row[p];
+        const longlong2 b = p + WR_THREADS < L2 ? row[p + WR_THREADS] : make_longlong2(0, 0);
+        take(a.x);
+        take(a.y);
+        take(b.x);
+        take(b.y);
     }
     nz = block_sum_ll(nz, shl);
     const double nrm = sqrt(block_sum_fixed(ss, sh));
@@ -555,7 +566,7 @@ __global__ void __launch_bounds__(WR_THREADS) k_acc_rows2(
     double inv_scale, const int64_t *coff_old, const int32_t *cterm_old, const float *cval_old,
     const double *snorm_new, const int64_t *coff_new, int32_t *cterm_new, float *cval_new, int32_t *cclu_new,
     int64_t cap, unsigned long long *error) {
-    constexpr int PER = 4;  // sub-chunks of WR_THREADS entries per chunk
+    constexpr int PER = 2;  // sub-chunks of WR_THREADS entry pairs per chunk
     constexpr int NWR = WR_THREADS / 32;
     __shared__ int warp_n[PER][NWR];
     const int j = blockIdx.x;
@@ -573,28 +584,32 @@ __global__ void __launch_bounds__(WR_THREADS) k_acc_rows2(
         }
         return;
     }
-    const int64_t base = acc_off[j], L = acc_off[j + 1] - base;
+    const int64_t base = acc_off[j], L2 = (acc_off[j + 1] - base) >> 1;  // entry pairs (even rows)
+    const longlong2 *row = reinterpret_cast<const longlong2 *>(acc + base);
     const int32_t doff = clu_doff[j];
     const double f = inv_scale / snorm_new[j];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned below = (1u << lane) - 1u;
     int64_t o = o0;
-    for (int64_t c0 = 0; c0 < L; c0 += (int64_t)WR_THREADS * PER) {
-        // sub-chunk m holds entries c0 + m*WR_THREADS + tid (coalesced loads)
-        long long v[PER];
-        unsigned bal[PER];
+    for (int64_t c0 = 0; c0 < L2; c0 += (int64_t)WR_THREADS * PER) {
+        // sub-chunk m holds pairs c0 + m*WR_THREADS + tid (coalesced 16-byte loads);
+        // entries keep their order: pair by pair, and x before y inside a pair
+        longlong2 v[PER];
+        int ex[PER];
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
-            const int64_t t = c0 + (int64_t)m * WR_THREADS + threadIdx.x;
-            v[m] = t < L ? acc[base + t] : 0;
-            bal[m] = __ballot_sync(0xffffffffu, v[m] != 0);
-        }
-        if (lane == 0) {
+            const int64_t p = c0 + (int64_t)m * WR_THREADS + threadIdx.x;
+            v[m] = p < L2 ? row[p] : make_longlong2(0, 0);
+            const int n = (v[m].x != 0) + (v[m].y != 0);
+            int inc = n;
 #pragma unroll
-            for (int m = 0; m < PER; ++m) warp_n[m][warp] = __popc(bal[m]);
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, d);
+                if (lane >= d) inc += y;
+            }
+            ex[m] = inc - n;
+            if (lane == 31) warp_n[m][warp] = inc;
         }
         __syncthreads();
-        // entries before (m, warp): all of sub-chunks < m, warps < warp of m
         int total = 0;
 #pragma unroll
         for (int m = 0; m < PER; ++m)
@@ -602,18 +617,23 @@ __global__ void __launch_bounds__(WR_THREADS) k_acc_rows2(
             for (int w = 0; w < NWR; ++w) total += warp_n[m][w];
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
-            if (v[m]) {
-                int pre = 0;
-                for (int mm = 0; mm < m; ++mm)
-                    for (int w = 0; w < NWR; ++w) pre += warp_n[mm][w];
-                for (int w = 0; w < warp; ++w) pre += warp_n[m][w];
-                const int64_t p = o + pre + __popc(bal[m] & below);
-                const int64_t t = c0 + (int64_t)m * WR_THREADS + threadIdx.x;
+            if (v[m].x == 0 && v[m].y == 0) continue;
+            int pre = 0;
+            for (int mm = 0; mm < m; ++mm)
+                for (int w = 0; w < NWR; ++w) pre += warp_n[mm][w];
+            for (int w = 0; w < warp; ++w) pre += warp_n[m][w];
+            int64_t pos = o + pre + ex[m];
+            const int64_t t = 2 * (c0 + (int64_t)m * WR_THREADS + threadIdx.x);
+            const long long pv[2] = {v[m].x, v[m].y};
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                if (!pv[e]) continue;
                 if (!over) {
-                    cterm_new[p] = (int32_t)t + doff;
-                    cval_new[p] = (float)((double)v[m] * f);
-                    cclu_new[p] = j;
+                    cterm_new[pos] = (int32_t)(t + e) + doff;
+                    cval_new[pos] = (float)((double)pv[e] * f);
+                    cclu_new[pos] = j;
                 }
+                ++pos;
             }
         }
         o += total;
