@@ -393,11 +393,13 @@ def test_relaxed_filter_lockstep(precision, case):
         s.close()
 
 
-def test_k_above_65536_uses_32_bit_ids_and_global_scores():
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
+def test_k_above_65536_uses_32_bit_ids_and_global_scores(precision):
     """k = 66,000 clusters (over the 16-bit id range, and a score vector too
-    large for shared memory): 32-bit scan ids and per-CTA score slabs in
-    global memory, against the oracle."""
+    large for shared memory): 32-bit scan ids (with FP32 values, or 16-bit
+    values in their own array) and per-CTA score slabs in global memory,
+    against the oracle."""
     c = generate(70_000, 400_000, 0.6, float(np.log(8.0)), 0.3, 5, 16, 77)
     ini = init_ids(c.N, 66_000, 78)
-    recs = lockstep(c, 66_000, ini, 3)
+    recs = lockstep(c, 66_000, ini, 3, precision=precision)
     assert recs[0]["stats"]["assign_global"] == 1
