@@ -211,9 +211,27 @@ def cpu_baseline(w, c, ini, iters, icp=1):
             break
         o.update()
     dt = time.perf_counter() - t0
-    return {"value": w.N * done / dt, "unit": "objects/s", "cores": Oracle.threads(), "kind": "oracle",
-            "sample": f"first {done} Lloyd iterations (assign+update) of the same corpus, FP64 oracle, "
-                      f"{dt:.1f} s", "sec_per_iter": dt / done}
+    cores = Oracle.threads()
+    out = {"value": w.N * done / dt, "unit": "objects/s", "cores": cores, "kind": "oracle",
+           "sample": f"first {done} Lloyd iterations (assign+update) of the same corpus, FP64 oracle, "
+                     f"{dt:.1f} s", "sec_per_iter": dt / done}
+    # one thread, first iteration only (bounded): the per-core figure
+    o1 = Oracle(c, w.k, ini, icp=icp, threads=1)
+    try:
+        t1 = time.perf_counter()
+        o1.assign()
+        o1.update()
+        d1 = time.perf_counter() - t1
+    finally:
+        Oracle(c, w.k, ini, icp=icp, threads=cores)  # restore the thread count
+    t0 = time.perf_counter()
+    o2 = Oracle(c, w.k, ini, icp=icp)
+    o2.assign()
+    o2.update()
+    d2 = time.perf_counter() - t0
+    out["single_thread"] = {"value": w.N / d1, "unit": "objects/s", "sample": "iteration 1, one thread",
+                            "same_sample_all_cores": w.N / d2}
+    return out
 
 
 def run_reference(args, w):
