@@ -53,3 +53,43 @@ def test_product_path_does_not_import_the_oracle():
                 text = open(os.path.join(root, f)).read()
                 assert "oracle" not in re.findall(r"import\s+(\w+)", text)
                 assert "from oracle" not in text and "import oracle" not in text
+
+
+def _struct_fields(name):
+    """Member names, in order, of `typedef struct { ... } name;` in sivf.h."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    m = re.search(r"typedef struct\s*\{([^{}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if decl:
+            fields.append(re.findall(r"(\w+)\s*$", decl)[0])
+    return fields
+
+
+def test_binding_structs_match_the_header():
+    """The ctypes mirrors of sivf_config, sivf_stats and sivf_instance_desc
+    list the header's members in the header's order (a mismatch would shift
+    every later member)."""
+    from paper_2103_16141_gb300 import sivf as S
+    for cname, cls in [("sivf_config", S.sivf_config), ("sivf_stats", S.sivf_stats),
+                       ("sivf_instance_desc", S.sivf_instance_desc)]:
+        assert [f for f, _ in cls._fields_] == _struct_fields(cname), cname
+
+
+def test_binding_struct_sizes_match_the_compiler():
+    """sizeof of each struct as gcc lays it out from the header equals the
+    ctypes size."""
+    import subprocess
+    import tempfile
+    from paper_2103_16141_gb300 import sivf as S
+    src = ('#include <stdio.h>\n#include "sivf.h"\nint main(void){printf("%zu %zu %zu\\n", sizeof(sivf_config), '
+           'sizeof(sivf_stats), sizeof(sivf_instance_desc));return 0;}\n')
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "s.c")
+        exe = os.path.join(d, "s")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), "-o", exe, c])
+        sizes = [int(x) for x in subprocess.check_output([exe]).split()]
+    assert sizes == [ctypes.sizeof(S.sivf_config), ctypes.sizeof(S.sivf_stats), ctypes.sizeof(S.sivf_instance_desc)]
