@@ -526,12 +526,15 @@ __global__ void __launch_bounds__(WR_THREADS) k_acc_rows1(
     double ss = 0.0;
     // rows start at even entries and have even lengths: 16-byte loads, two
     // of them in flight per thread
+    // FP64 is a slow pipe on this GPU: sum v^2 and v * u on the integers'
+    // doubles and apply the power-of-two scale once at the end (exact, so the
+    // results are the same as scaling every term)
     const longlong2 *row = reinterpret_cast<const longlong2 *>(acc + base);
     const int64_t L2 = L >> 1;
     auto take = [&](long long v) {
         if (v) {
             ++nz;
-            const double x = (double)v * inv_scale;
+            const double x = (double)v;
             ss += x * x;
         }
     };
@@ -544,12 +547,12 @@ __global__ void __launch_bounds__(WR_THREADS) k_acc_rows1(
         take(b.y);
     }
     nz = block_sum_ll(nz, shl);
-    const double nrm = sqrt(block_sum_fixed(ss, sh));
+    const double nrm = sqrt(block_sum_fixed(ss, sh) * (inv_scale * inv_scale));
     double dot = 0.0;
     const int32_t doff = clu_doff[j];
     for (int64_t q = cb + threadIdx.x; q < ce; q += WR_THREADS)
-        dot += (double)acc[base + (cterm_old[q] - doff)] * inv_scale * (double)cval_old[q];
-    dot = block_sum_fixed(dot, sh);
+        dot += (double)acc[base + (cterm_old[q] - doff)] * (double)cval_old[q];
+    dot = block_sum_fixed(dot, sh) * inv_scale;
     if (threadIdx.x == 0) {
         sz[j] = nz;
         snorm_new[j] = nrm;
