@@ -93,3 +93,23 @@ def test_binding_struct_sizes_match_the_compiler():
         subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), "-o", exe, c])
         sizes = [int(x) for x in subprocess.check_output([exe]).split()]
     assert sizes == [ctypes.sizeof(S.sivf_config), ctypes.sizeof(S.sivf_stats), ctypes.sizeof(S.sivf_instance_desc)]
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    """Without a CUDA device the binding refuses to run (there is no CPU
+    path): creating a context raises instead of computing anything."""
+    import numpy as np
+    import pytest
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2103_16141_gb300 import SIVF
+    from tests.helpers import random_dense_corpus
+    _, c = random_dense_corpus(20, 10, 0.5, seed=1)
+    with pytest.raises(Exception):
+        SIVF(c.row_ptr, c.idx, c.val, c.D, 2, np.array([0, 1], dtype=np.int32))
+
+
+def test_icp_mode_names():
+    from paper_2103_16141_gb300.sivf import icp_mode
+    assert [icp_mode(x) for x in (False, True, 0, 1, 2, 3, "cbicp", "relaxed")] == [0, 1, 0, 1, 2, 3, 2, 3]
