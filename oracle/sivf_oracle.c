@@ -455,6 +455,9 @@ int orc_set_labels(orc *o, const int32_t *labels) {
     for (int64_t i = 0; i < o->N; ++i) {
         if (o->labels[i] != labels[i]) {
             o->labels[i] = labels[i];
+            /* its stored score belongs to the old cluster (the new one is
+             * marked moving below, so the object is not filtered next time
+             * in any case) */
             o->own_ok[i] = 0;
         }
     }

@@ -29,6 +29,8 @@ MUTANTS = [
     ("update_objective_of_mean", "snorm[j] = sqrt(ss);", "snorm[j] = sqrt(ss) / (double)cnt;"),
     ("cbicp_branch_inverted", "if (o->lambda[o->if_cid[q]] == 0) rho", "if (o->lambda[o->if_cid[q]] == 1) rho"),
     ("relaxed_test_inverted", "if (rho[a_prev] >= o->own[i]) break;", "if (rho[a_prev] < o->own[i]) break;"),
+    ("set_labels_new_cluster_not_moving", "            o->lambda[a1] = 0;\n        }\n    }\n    return 0;",
+     "        }\n    }\n    return 0;"),
     ("unfiltered_when_invariant", "int filt = o->icp && a_prev >= 0 && o->own_ok[i] && o->lambda[a_prev] == 1;",
      "int filt = o->icp && a_prev >= 0 && o->own_ok[i] && o->lambda[a_prev] == 0;"),
 ]
@@ -47,6 +49,7 @@ def _battery(lib):
     for s in (3, 4):
         pins.pin_cbicp(s, lib)
     pins.pin_relaxed(0, lib)
+    pins.pin_set_labels(lib)
 
 
 def _compile(src_text: str, out_dir: str, name: str):

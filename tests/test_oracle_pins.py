@@ -440,3 +440,43 @@ def pin_zero_scores(lib=None):
     assert lab[1] == 0 and lab[2] == 1
     hist = o.run(10)
     assert hist[-1][0].changed == 0
+
+
+def test_set_labels_resync_semantics():
+    """Reading R12: pushing the labels the oracle already holds changes
+    nothing (same trajectory as an untouched twin); moving one object marks
+    both of its clusters moving, on top of the assignment's own changes, and
+    the object loses its stored own score, so it is not filtered next time."""
+    pin_set_labels()
+
+
+def pin_set_labels(lib=None):
+    w = CONFIGS["c1"].scaled(N=600, D=1500, k=12)
+    c = generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, 41)
+    ini = init_ids(w.N, w.k, 41)
+    a, b = Oracle(c, w.k, ini, icp=True, lib=lib), Oracle(c, w.k, ini, icp=True, lib=lib)
+    for _ in range(3):
+        a.assign(), b.assign()
+        a.update(), b.update()
+    a.assign(), b.assign()
+    b.set_labels(b.labels())  # a no-op push
+    assert np.array_equal(a.lam(), b.lam())
+    for _ in range(3):
+        ua, ub = a.update(), b.update()
+        assert ua.objective == ub.objective
+        aa, ab = a.assign(), b.assign()
+        assert np.array_equal(a.labels(), b.labels()) and aa.filtered == ab.filtered
+    # move one object of an invariant cluster to another invariant cluster
+    lam, lab = b.lam(), b.labels()
+    inv = np.nonzero(lam == 1)[0]
+    assert len(inv) >= 2
+    i = int(np.nonzero(lab == inv[0])[0][0])
+    new = lab.copy()
+    new[i] = inv[1]
+    b.set_labels(new)
+    lam2 = b.lam()
+    assert lam2[inv[0]] == 0 and lam2[inv[1]] == 0
+    assert np.all(lam2[lam == 0] == 0)  # the assignment's moving clusters stay moving
+    b.update()
+    b.assign()
+    assert not b.scores()[2][i]  # own score dropped: not filtered
