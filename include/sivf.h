@@ -162,7 +162,8 @@ sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t
 sivf_status sivf_reseed(sivf_ctx *ctx, const int32_t *init_ids);
 
 /*
- * sivf_assign — one assignment step (Algorithm 4; Algorithm 2 when icp = 0):
+ * sivf_assign — one assignment step (Algorithm 4; Algorithm 2 when icp = 0,
+ * Algorithm 3 when icp = 2, Algorithm 4 with the relaxed filter when icp = 3):
  * scores every object against the structured inverted file, takes the argmax
  * (largest score, lowest index on ties), and marks invariant clusters
  * (lambda_j^[r] = 1 iff no object entered or left cluster j).
@@ -215,7 +216,8 @@ sivf_status sivf_get_centroids(sivf_ctx *ctx, int64_t *off, int32_t *term, float
                                int64_t *nnz_out);
 
 /*
- * sivf_get_inverted_file — the structured inverted file (Algorithm 5 output):
+ * sivf_get_inverted_file — the structured inverted file (Algorithm 5 output;
+ * with icp = 2 the unstructured file of Algorithm 3, one part per list):
  *   off : HOST int64[D+1], mf0 : HOST int32[D] (front length),
  *   cid : HOST int32[cap], u : HOST float[cap] (FP32 values), nnz_out.
  * Same capacity rule as sivf_get_centroids.
