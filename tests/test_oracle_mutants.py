@@ -10,6 +10,7 @@ import subprocess
 import pytest
 
 from oracle.sivf_oracle import _SRC, bind
+from tests import test_golden as golden
 from tests import test_oracle_pins as pins
 
 # (name, text in sivf_oracle.c, replacement); every mutant stays memory-safe
@@ -33,6 +34,10 @@ MUTANTS = [
      "        }\n    }\n    return 0;"),
     ("unfiltered_when_invariant", "int filt = o->icp && a_prev >= 0 && o->own_ok[i] && o->lambda[a_prev] == 1;",
      "int filt = o->icp && a_prev >= 0 && o->own_ok[i] && o->lambda[a_prev] == 0;"),
+    ("empty_cluster_zeroed", "nval[d] = o->cen_val[q];", "nval[d] = 0.0;"),
+    ("relaxed_tried_always", "2 * n_moving_prev <= k", "n_moving_prev <= k"),
+    ("runner_up_not_tracked", "} else if (x > snd) {", "} else if (0) {"),
+    ("filtered_counted_as_k", "simcalc += (filt || relax) ? n_moving_prev : k;", "simcalc += k;"),
 ]
 
 
@@ -50,6 +55,7 @@ def _battery(lib):
         pins.pin_cbicp(s, lib)
     pins.pin_relaxed(0, lib)
     pins.pin_set_labels(lib)
+    golden.pin_golden(lib)
 
 
 def _compile(src_text: str, out_dir: str, name: str):
