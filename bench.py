@@ -234,6 +234,16 @@ def cpu_baseline(w, c, ini, iters, icp=1):
     return out
 
 
+METRIC = "objects/s (Lloyd iterations of SIVF spherical k-means); sec per Lloyd iteration"
+ICP_NAMES = ["ivf", "sivf", "ivf-cbicp", "sivf-relaxed"]
+
+
+def workload_name(w, nnz: int) -> str:
+    """The workload as both arms name it in config.workload."""
+    return (f"{w.name}: N={w.N} D={w.D} nnz={nnz} k={w.k} zipf={w.zipf_s} "
+            f"len=lognormal({w.mu:.3f},{w.sigma}) clip[{w.lo},{w.hi}] seed={w.seed}")
+
+
 def run_reference(args, w):
     """Reference arm: the FP64 CPU oracle, each step one Lloyd iteration."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -258,11 +268,12 @@ def run_reference(args, w):
         step()
     dt = time.perf_counter() - t0
     value = w.N * args.steps / dt
-    line = {"metric": "objects/s (Lloyd iterations of SIVF spherical k-means)", "value": value, "unit": "objects/s",
+    line = {"metric": METRIC, "value": value, "unit": "objects/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"{w.name}: N={w.N} D={w.D} k={w.k} zipf={w.zipf_s}", "iters_per_step": 1},
+            "config": {"workload": workload_name(w, c.nnz), "icp": ICP_NAMES[args.icp], "max_iter": w.max_iter,
+                       "iters_per_step": 1},
             "cpu_baseline": {"value": value, "unit": "objects/s", "cores": Oracle.threads(), "kind": "oracle",
                              "sample": f"iterations {args.warmup + 1}..{args.warmup + args.steps} of the corpus"},
             "e2e": {"value": value, "unit": "objects/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -459,14 +470,13 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "objects/s (Lloyd iterations of SIVF spherical k-means); sec per Lloyd iteration",
+            "metric": METRIC,
             "value": value, "unit": "objects/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if w.precision == "fp32" else f"{w.precision}-postings/f32-products/fixed-point-sum",
             "data": "synthetic",
-            "config": {"workload": f"{w.name}: N={w.N} D={w.D} nnz={c.nnz} k={w.k} zipf={w.zipf_s} "
-                                   f"len=lognormal({w.mu:.3f},{w.sigma}) clip[{w.lo},{w.hi}] seed={w.seed}",
-                       "precision": w.precision, "icp": ["ivf", "sivf", "ivf-cbicp", "sivf-relaxed"][args.icp], "max_iter": w.max_iter,
+            "config": {"workload": workload_name(w, c.nnz),
+                       "precision": w.precision, "icp": ICP_NAMES[args.icp], "max_iter": w.max_iter,
                        "iters_per_step": iters_per_step, "sec_per_iter": ms / 1e3 / tot_iters,
                        "l2": f"inputs larger than L2: every assignment streams the object CSR "
                              f"({(c.nnz * 8 + (w.N + 1) * 8) / 1e9:.2f} GB); the inverted file is reused from L2 "
