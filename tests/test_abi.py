@@ -113,3 +113,67 @@ def test_no_cpu_fallback_without_a_gpu():
 def test_icp_mode_names():
     from paper_2103_16141_gb300.sivf import icp_mode
     assert [icp_mode(x) for x in (False, True, 0, 1, 2, 3, "cbicp", "relaxed")] == [0, 1, 0, 1, 2, 3, 2, 3]
+
+
+def test_init_rejects_bad_arguments_before_touching_the_device():
+    """sivf_init and sivf_batch_init check sizes, pointers, configuration and
+    seed ids on the host before any CUDA call: every rejection below returns
+    its status and leaves *out NULL, with no GPU present."""
+    import numpy as np
+    from paper_2103_16141_gb300 import sivf as S
+    lib = ctypes.CDLL(_build.build())
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    lib.sivf_init.argtypes = [ctypes.POINTER(vp), vp, i64, i32, i32, vp, vp, vp, vp, vp]
+    lib.sivf_batch_init.argtypes = [ctypes.POINTER(vp), vp, i32, vp, vp]
+    INVALID, BAD_CSR = 1, 2
+
+    row_ptr = np.array([0, 1, 2, 3, 4], dtype=np.int64)
+    idx = np.zeros(4, dtype=np.int32)
+    val = np.ones(4, dtype=np.float32)
+    seeds = np.array([0, 1], dtype=np.int32)
+    P = lambda a: a.ctypes.data  # noqa: E731
+
+    def init(cfg=None, N=4, D=3, k=2, rp=P(row_ptr), ix=P(idx), vl=P(val), ini=P(seeds), out=True):
+        h = vp(12345)
+        st = lib.sivf_init(ctypes.byref(h) if out else None, ctypes.byref(cfg) if cfg else None,
+                           N, D, k, rp, ix, vl, ini, None)
+        if out:
+            assert h.value is None, "out must be cleared on failure"
+        return st
+
+    def cfg(**kw):
+        c = S.sivf_config()
+        c.prec, c.icp = 0, 1
+        for key, v in kw.items():
+            setattr(c, key, v)
+        return c
+
+    assert init(out=False) == INVALID
+    for kw in [dict(N=0), dict(D=0), dict(k=0), dict(k=5), dict(N=1 << 31), dict(D=(1 << 30) + 1),
+               dict(rp=None), dict(ix=None), dict(vl=None), dict(ini=None)]:
+        assert init(**kw) == INVALID, kw
+    for kw in [dict(prec=3), dict(prec=-1), dict(icp=4), dict(icp=-1)]:
+        assert init(cfg(**kw)) == INVALID, kw
+    for bad in ([0, 0], [0, 4], [-1, 1]):
+        assert init(ini=P(np.array(bad, dtype=np.int32))) == INVALID, bad
+    # host inputs: the CSR header is read on the host first
+    shifted = np.array([1, 2, 3, 4, 5], dtype=np.int64)
+    assert init(cfg(inputs_on_host=1), rp=P(shifted)) == BAD_CSR
+
+    def batch(descs, c=None, n=None):
+        arr = (S.sivf_instance_desc * max(len(descs), 1))(*descs)
+        h = vp(12345)
+        st = lib.sivf_batch_init(ctypes.byref(h), ctypes.byref(c) if c else None,
+                                 len(descs) if n is None else n, ctypes.addressof(arr), None)
+        assert h.value is None
+        return st
+
+    def desc(N=4, D=3, k=2, ini=seeds):
+        return S.sivf_instance_desc(N, D, k, P(row_ptr), P(idx), P(val), P(ini))
+
+    assert batch([desc()], n=0) == INVALID
+    assert batch([desc()], n=65537) == INVALID
+    assert batch([desc()], c=cfg(inputs_on_host=1)) == INVALID
+    assert batch([desc()], c=cfg(icp=5)) == INVALID
+    assert batch([desc(), desc(k=5)]) == INVALID
+    assert batch([desc(), desc(ini=np.array([1, 1], dtype=np.int32))]) == INVALID
