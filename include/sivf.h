@@ -114,8 +114,11 @@ typedef struct {
     int64_t moved_nnz;       /* object non-zeros the last update read: sort form, every member
                                 of a recomputed cluster; dense form, the objects whose label
                                 changed, counted once per cluster row touched */
-    double objective_assign; /* J^[r] = sum_i <x_i, mu_{a(i)}^[r-1]> (FP64) */
-    double objective_update; /* sum_j ||s_j^[r]||, s_j = sum of members (FP64) */
+    double objective_assign; /* J^[r] = sum_i <x_i, mu_{a(i)}^[r-1]> (FP64) for the labels of
+                                assignment r, evaluated by the update step that follows it as
+                                sum_j <s_j, mu_j^[r-1]>: current after sivf_update, still the
+                                previous value between sivf_assign and sivf_update */
+    double objective_update; /* sum_j ||s_j^[r]||, s_j = sum of members (FP64), of the last update */
     double ms_assign;        /* device time of the last assignment step */
     double ms_update;        /* device time of the last update step */
     int64_t launches;        /* kernels launched by the library since sivf_init / sivf_reseed */
@@ -189,7 +192,9 @@ sivf_status sivf_update(sivf_ctx *ctx);
  * iterations after the second run inside one CUDA graph (per-step device
  * times in sivf_stats are then those of the last host-launched step).
  *   iters_out     : HOST out, may be NULL; assignment steps run by this call.
- *   objective_out : HOST out, may be NULL; J of the last assignment.
+ *   objective_out : HOST out, may be NULL; sum_j ||s_j|| of the last update
+ *                   (the objective with the final centroids). At convergence
+ *                   it equals J of the last assignment, which kept every label.
  */
 sivf_status sivf_run(sivf_ctx *ctx, int32_t max_iter, int32_t *iters_out, double *objective_out);
 

@@ -722,6 +722,7 @@ static sivf_status run_loop(sivf_ctx *c, int32_t max_iter, std::vector<int32_t> 
     if (c->needs_update && max_iter > 0) {
         st = sivf_update(c);
         if (st != SIVF_OK) return st;
+        for (size_t m = 0; m < ni; ++m) objf[m] = c->inst_obj_update_h[m];
     }
     while (c->iter < max_total && remaining > 0) {
         if (c->cfg.use_graph && c->iter >= 2 && !c->needs_update) {
@@ -754,7 +755,7 @@ sivf_status sivf_run(sivf_ctx *c, int32_t max_iter, int32_t *iters_out, double *
     if (max_iter < 0) return fail(c, SIVF_ERR_INVALID_ARG, "max_iter < 0");
     const int32_t iter0 = c->iter;
     std::vector<int32_t> done((size_t)c->n_inst, 0);
-    std::vector<double> objf((size_t)c->n_inst, 0.0);
+    std::vector<double> objf(c->inst_obj_update_h);  // a call that runs no update reports the last one
     st = run_loop(c, max_iter, done, objf);
     if (st != SIVF_OK) return st;
     if (iters_out) *iters_out = c->n_inst == 1 && done[0] ? done[0] - iter0 : c->iter - iter0;
@@ -862,7 +863,7 @@ sivf_status sivf_batch_run(sivf_ctx *c, int32_t max_iter, int32_t *iters_out, do
     if (max_iter < 0) return fail(c, SIVF_ERR_INVALID_ARG, "max_iter < 0");
     const size_t ni = (size_t)c->n_inst;
     std::vector<int32_t> done(ni, 0);
-    std::vector<double> objf(ni, 0.0);
+    std::vector<double> objf(c->inst_obj_update_h);  // a call that runs no update reports the last one
     st = run_loop(c, max_iter, done, objf);
     if (st != SIVF_OK) return st;
     for (size_t m = 0; m < ni; ++m) {
