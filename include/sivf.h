@@ -276,8 +276,10 @@ sivf_status sivf_batch_init(sivf_ctx **out, const sivf_config *cfg, int32_t n_in
  * instance has had an assignment (r > 1) that changes none of its labels, or
  * max_iter assignments. An instance that converged stays converged (all its
  * clusters are invariant, so its objects keep their labels at no scan cost).
- *   iters_out     : HOST int32[n_inst], may be NULL; assignment steps until the
- *                   instance converged (max_iter if it did not).
+ *   iters_out     : HOST int32[n_inst], may be NULL; the iteration r at which
+ *                   the instance converged, counted from sivf_batch_init or
+ *                   sivf_reseed (not from this call), or the context's
+ *                   iteration count if it has not converged.
  *   objective_out : HOST double[n_inst], may be NULL; the instance's objective
  *                   sum of cosines at its last update.
  */
