@@ -38,6 +38,10 @@ MUTANTS = [
     ("relaxed_tried_always", "2 * n_moving_prev <= k", "n_moving_prev <= k"),
     ("runner_up_not_tracked", "} else if (x > snd) {", "} else if (0) {"),
     ("filtered_counted_as_k", "simcalc += (filt || relax) ? n_moving_prev : k;", "simcalc += k;"),
+    ("score_objects_ties_to_highest", "if (rho[j] > bst) { snd = bst; bst = rho[j]; a = j; }",
+     "if (rho[j] >= bst) { snd = bst; bst = rho[j]; a = j; }"),
+    ("score_objects_runner_up_skips_ties", "else if (rho[j] > snd) snd = rho[j];",
+     "else if (rho[j] > snd && rho[j] < bst) snd = rho[j];"),
 ]
 
 
@@ -55,6 +59,7 @@ def _battery(lib):
         pins.pin_cbicp(s, lib)
     pins.pin_relaxed(0, lib)
     pins.pin_set_labels(lib)
+    pins.pin_score_objects(0, lib)
     golden.pin_golden(lib)
 
 

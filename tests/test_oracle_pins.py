@@ -61,6 +61,33 @@ def pin_brute_force(seed, icp, lib=None):
         o.update()
 
 
+@pytest.mark.parametrize("seed", SMALL_SEEDS[:4])
+def test_score_objects_equals_dense_brute_force(seed):
+    """The per-object scoring used for sampled checks at full size (Algorithm 2
+    scoring without state change) equals the dense definition bit for bit:
+    label (lowest index on ties), best and second-best score, for objects in
+    any order, against seed centroids holding an exact tie (two identical
+    documents) and against updated centroids."""
+    pin_score_objects(seed)
+
+
+def pin_score_objects(seed, lib=None):
+    X, c, _ = _small(seed)
+    ini = np.array([0, c.N - 1, 5, 9, 14], dtype=np.int32)  # rows 0 and N-1 are identical
+    o = Oracle(c, 5, ini, icp=True, lib=lib)
+    ids = np.random.default_rng(seed).permutation(c.N).astype(np.int64)
+    for step in range(3):
+        lab_bf, rho = brute_force_scores(X, o.dense_centroids())
+        lab, best, second = o.score_objects(ids)
+        assert np.array_equal(lab, lab_bf[ids])
+        assert np.array_equal(best, rho[ids, lab_bf[ids]])
+        assert np.array_equal(second, np.sort(rho, axis=1)[ids, -2])
+        if step == 0:
+            assert np.any(rho[:, 0] == rho[:, 1]) and lab_bf[0] == 0 and lab_bf[c.N - 1] == 0
+        o.assign()
+        o.update()
+
+
 @pytest.mark.parametrize("seed", SMALL_SEEDS)
 def test_update_is_normalised_mean_of_members(seed):
     """Algorithm 5 lines 17-20 then unit length: mu_j = s_j / ||s_j||, support =
