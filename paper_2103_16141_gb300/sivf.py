@@ -200,6 +200,17 @@ def sivf_destroy(ctx: int) -> None:
         load().sivf_destroy(ctx)
 
 
+def _check_csr_sizes(row_ptr, idx, val) -> None:
+    """The library reads row_ptr[N] and then that many idx and val entries:
+    the arrays must hold them (a short array would be read past its end)."""
+    n = len(row_ptr)
+    if n < 2:
+        raise ValueError("row_ptr must hold N + 1 >= 2 offsets")
+    nnz = int(row_ptr[n - 1])
+    if len(idx) != nnz or len(val) != nnz:
+        raise ValueError(f"idx and val must hold row_ptr[N] = {nnz} entries (got {len(idx)}, {len(val)})")
+
+
 class SIVF:
     """One clustering instance on the current CUDA device.
 
@@ -240,16 +251,21 @@ class SIVF:
             # nothing is borrowed: the library copies the host arrays at init
             (rp, rp_p), (ix, ix_p), (vl, vl_p) = (host(row_ptr, torch.int64), host(idx, torch.int32),
                                                   host(val, torch.float32))
+            _check_csr_sizes(rp, ix, vl)
             self.row_ptr = self.idx = self.val = None
             self.N = int(len(rp) - 1)
         else:
             self.row_ptr = to_dev(row_ptr, torch.int64)
             self.idx = to_dev(idx, torch.int32)
             self.val = to_dev(val, torch.float32)
+            _check_csr_sizes(self.row_ptr, self.idx, self.val)
             rp_p, ix_p, vl_p = self.row_ptr.data_ptr(), self.idx.data_ptr(), self.val.data_ptr()
             self.N = int(self.row_ptr.numel() - 1)
         self.D, self.k = int(D), int(k)
+        self.device = dev
         ini = np.ascontiguousarray(np.asarray(init_ids, dtype=np.int32))
+        if ini.shape != (self.k,):  # the library reads k ids
+            raise ValueError(f"init_ids must hold k = {self.k} ids")
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         cfg = sivf_config(PRECISIONS[precision], icp_mode(icp), int(threads), int(ctas_per_sm), int(mem_cap_bytes),
                           int(bool(use_graph)), int(bool(autotune)), SCORE_BUFFERS[score_buffer],
@@ -270,6 +286,8 @@ class SIVF:
     def reseed(self, init_ids) -> None:
         import numpy as np
         ini = np.ascontiguousarray(np.asarray(init_ids, dtype=np.int32))
+        if ini.shape != (self.k,):  # the library reads k ids
+            raise ValueError(f"init_ids must hold k = {self.k} ids")
         sivf_reseed(self.ctx, ini.ctypes.data)
 
     def assign(self) -> int:
@@ -294,20 +312,31 @@ class SIVF:
         return out
 
     def labels_device(self, out=None):
+        """Labels into a device tensor (int32[N] on the context's device; a new
+        one if out is None). The library writes N int32 values, so out is
+        checked first."""
         import torch
         if out is None:
-            out = torch.empty(self.N, dtype=torch.int32, device=self.row_ptr.device)
+            out = torch.empty(self.N, dtype=torch.int32, device=self.device)
+        elif (not isinstance(out, torch.Tensor) or out.device != self.device or out.dtype != torch.int32
+              or not out.is_contiguous() or out.numel() != self.N):
+            raise ValueError(f"out must be a contiguous int32 tensor of {self.N} elements on {self.device}")
         sivf_get_labels(self.ctx, out.data_ptr(), True)
         return out
 
     def set_labels(self, labels) -> None:
         import numpy as np
         import torch
+        # the library reads N labels from the pointer it is given
         if isinstance(labels, torch.Tensor) and labels.is_cuda:
-            t = labels.to(torch.int32).contiguous()
+            t = labels.to(device=self.device, dtype=torch.int32).contiguous()
+            if t.shape != (self.N,):
+                raise ValueError(f"labels must hold N = {self.N} entries")
             sivf_set_labels(self.ctx, t.data_ptr(), True)
         else:
             a = np.ascontiguousarray(np.asarray(labels, dtype=np.int32))
+            if a.shape != (self.N,):
+                raise ValueError(f"labels must hold N = {self.N} entries")
             sivf_set_labels(self.ctx, a.ctypes.data, False)
 
     def lam(self):
@@ -377,13 +406,19 @@ class SIVFBatch:
         import torch
 
         dev = torch.device("cuda", torch.cuda.current_device())
+        corpora, ks, init_ids = list(corpora), list(ks), list(init_ids)
+        if not (len(corpora) == len(ks) == len(init_ids)):
+            raise ValueError("corpora, ks and init_ids must have one entry per instance")
         self._keep = []
         descs = []
         for c, k, ini in zip(corpora, ks, init_ids):
             rp = torch.as_tensor(np.ascontiguousarray(c.row_ptr), dtype=torch.int64).to(dev)
             ix = torch.as_tensor(np.ascontiguousarray(c.idx), dtype=torch.int32).to(dev)
             vl = torch.as_tensor(np.ascontiguousarray(c.val), dtype=torch.float32).to(dev)
+            _check_csr_sizes(rp, ix, vl)
             ii = np.ascontiguousarray(np.asarray(ini, dtype=np.int32))
+            if ii.shape != (int(k),):  # the library reads k ids
+                raise ValueError(f"init_ids of an instance must hold its k = {int(k)} ids")
             self._keep.append((rp, ix, vl, ii))
             descs.append(sivf_instance_desc(int(rp.numel() - 1), int(c.D), int(k), rp.data_ptr(), ix.data_ptr(),
                                             vl.data_ptr(), ii.ctypes.data))

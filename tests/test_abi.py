@@ -177,3 +177,32 @@ def test_init_rejects_bad_arguments_before_touching_the_device():
     assert batch([desc()], c=cfg(icp=5)) == INVALID
     assert batch([desc(), desc(k=5)]) == INVALID
     assert batch([desc(), desc(ini=np.array([1, 1], dtype=np.int32))]) == INVALID
+
+
+def test_binding_checks_array_sizes_before_the_library_reads_them():
+    """The library reads row_ptr[N] idx and val entries, k seed ids and N
+    labels from the pointers it is given; the binding rejects shorter (or
+    longer) arrays and a label buffer of the wrong kind before any call."""
+    import numpy as np
+    import pytest
+    import torch
+    from paper_2103_16141_gb300 import sivf as S
+
+    rp = np.array([0, 2, 3], dtype=np.int64)
+    S._check_csr_sizes(rp, np.zeros(3, np.int32), np.ones(3, np.float32))
+    for ix, vl in [(2, 3), (3, 2), (4, 3)]:
+        with pytest.raises(ValueError):
+            S._check_csr_sizes(rp, np.zeros(ix, np.int32), np.ones(vl, np.float32))
+    with pytest.raises(ValueError):
+        S._check_csr_sizes(np.array([0], dtype=np.int64), np.zeros(0, np.int32), np.ones(0, np.float32))
+
+    class Ctx:  # stands in for a live context; no call reaches the library
+        N, k, ctx, device = 4, 2, None, torch.device("cuda", 0)
+
+    with pytest.raises(ValueError):
+        S.SIVF.set_labels(Ctx(), np.zeros(3, np.int32))
+    with pytest.raises(ValueError):
+        S.SIVF.reseed(Ctx(), [0])
+    for out in (torch.zeros(4, dtype=torch.int32), torch.zeros(4, dtype=torch.int64), [0, 0, 0, 0]):
+        with pytest.raises(ValueError):
+            S.SIVF.labels_device(Ctx(), out=out)

@@ -403,3 +403,42 @@ def test_k_above_65536_uses_32_bit_ids_and_global_scores(precision):
     ini = init_ids(c.N, 66_000, 78)
     recs = lockstep(c, 66_000, ini, 3, precision=precision)
     assert recs[0]["stats"]["assign_global"] == 1
+
+
+@pytest.mark.parametrize("inputs_on_host", [False, True])
+def test_device_label_buffers_equal_host_buffers(inputs_on_host):
+    """sivf_get_labels and sivf_set_labels with DEVICE buffers give what the
+    HOST buffers give: the labels copied into a device tensor equal the host
+    copy, and a twin context resynchronised from a device buffer reaches the
+    same lambda, centroids and next labels as one resynchronised from the
+    host (also for a context built from host inputs)."""
+    import torch
+    w = CONFIGS["c1"]
+    c, ini = corpus_for(w)
+    a = gpu_instance(c, w.k, ini, inputs_on_host=inputs_on_host)
+    b = gpu_instance(c, w.k, ini, inputs_on_host=inputs_on_host)
+    try:
+        for s in (a, b):
+            s.assign()
+            s.update()
+            s.assign()
+        lab = a.labels()
+        dl = a.labels_device()
+        assert dl.device == a.device and np.array_equal(dl.cpu().numpy(), lab)
+        out = torch.full((c.N,), -7, dtype=torch.int32, device=a.device)
+        assert a.labels_device(out) is out and np.array_equal(out.cpu().numpy(), lab)
+        moved = ((lab + 1) % w.k).astype(np.int32)  # every object changes cluster
+        a.set_labels(moved)
+        b.set_labels(torch.from_numpy(moved).to(b.device))
+        assert np.array_equal(a.labels(), moved) and np.array_equal(b.labels(), moved)
+        assert np.array_equal(a.lam(), b.lam())
+        a.update()
+        b.update()
+        for x, y in zip(a.centroids(), b.centroids()):
+            assert np.array_equal(x, y)
+        a.assign()
+        b.assign()
+        assert np.array_equal(a.labels(), b.labels())
+    finally:
+        a.close()
+        b.close()
