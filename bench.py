@@ -1,24 +1,33 @@
 #!/usr/bin/env python3
 """Benchmark of SIVF spherical k-means on GB300.
 
-Workload (default): the medium single-GPU corpus, N = 300,000 documents,
-D = 100,000 terms, Zipf s = 1.05, lognormal(5.0, 0.7) lengths clipped to
-[10, 3000] (~190 nnz/doc, 57M nnz), k = 1000, FP32 postings, ICP on.
+Workload (default): the largest single-GPU corpus, N = 8,000,000 documents,
+D = 140,000 terms, Zipf s = 1.1, lognormal lengths of mean 60 (sigma 0.8,
+clipped to [5, 3000]; 480M nnz, 3.84 GB CSR), k = 20,000, BF16 postings with
+the exact re-score, ICP on.
 
-A step is one complete clustering run from the seeded initial centroids:
-seeding + up to 50 Lloyd iterations (assignment, Algorithm 4, and update,
-Algorithm 5), every step identical. `value` = objects assigned per second
-(N * iterations / step time), inputs resident in HBM; `e2e` = the same metric
-through the C ABI with the corpus in pinned host memory and the labels copied
-back, every step.
+A step is one Lloyd iteration (assignment, Algorithm 4, then update,
+Algorithm 5) with the state carried from step to step: the W warm-up steps are
+iterations 1..W from the seeded centroids and the K timed steps are iterations
+W+1..W+K (the iteration cap of the workload does not stop the window). `value` =
+objects assigned per second (N * K / timed seconds), inputs resident in HBM,
+CUDA events on the library's stream. Beside it:
+  - vs_fp32: the same window with FP32 postings, in the same process (both
+    paths re-score every object whose top-2 margin lies inside their error
+    bound exactly, so their labels are the same at every iteration, checked);
+  - roofline of the assignment kernel for both paths, against the measured
+    L2-read or HBM peak, whichever serves most of its algorithmic bytes;
+  - e2e: the same window through the C ABI with the CSR copied from pinned
+    host memory and the labels read back, every step;
+  - cpu_baseline: the FP64 oracle on the host cores, on a bounded sample.
 
 --impl reference times the FP64 CPU oracle (the plain restatement of the
-method) on the host cores instead: each step is one Lloyd iteration of the
-same workload.
+method) on the same workload and window instead.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -35,47 +44,44 @@ if ROOT not in sys.path:
 
 from synth import CONFIGS, generate, init_ids  # noqa: E402
 
-# bytes per posting read by the scan: 16-bit id + value (k <= 65536), else 32-bit id + value
+# bytes per posting read by the sparse scan: 16-bit id + value (k <= 65536), else 32-bit id + value
 B_POST16 = {"fp32": 6, "bf16": 4, "fp16": 4}
 B_POST32 = {"fp32": 8, "bf16": 6, "fp16": 6}
+# bytes per entry of a dense head-term row
+B_DENSE = {"fp32": 4, "bf16": 2, "fp16": 2}
+L2_BYTES = 129 * 2**20  # GB300 L2
+METRIC = "objects/s (Lloyd iterations of SIVF spherical k-means); sec per Lloyd iteration"
+ICP_NAMES = ["ivf", "sivf", "ivf-cbicp", "sivf-relaxed"]
+REF_SAMPLE = 2048  # objects scored per sampled oracle step
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS) + ["c4"])
+    ap.add_argument("--config", default="c5", choices=sorted(CONFIGS) + ["c4"])
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--icp", type=int, default=1, choices=[0, 1, 2, 3],
                     help="1: SIVF (Algorithm 4); 0: unfiltered IVF (Algorithm 2); 2: IVF-CBICP (Algorithm 3); "
                          "3: SIVF with the relaxed filter")
-    ap.add_argument("--max-iter", type=int, default=None)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
-    ap.add_argument("--graph", type=int, default=1, help="1: iterations after the second run in one CUDA graph")
     ap.add_argument("--autotune", type=int, default=1, help="1: pick the assignment kernel configuration by timing")
+    ap.add_argument("--graph", type=int, default=1, help="c4 only: iterations after the second in one CUDA graph")
+    ap.add_argument("--max-iter", type=int, default=None, help="c4 only: iteration cap of each instance")
+    ap.add_argument("--dense-max-mb", type=float, default=0.0,
+                    help="device memory for dense head-term rows (0 = automatic, < 0 = none)")
+    ap.add_argument("--dense-min-fraction", type=float, default=0.0,
+                    help="list length / k from which a term gets a dense row (0 = automatic)")
+    ap.add_argument("--update-mode", default="auto", choices=["auto", "dense", "sort"],
+                    help="cluster sums of the update step (sort: no k x D accumulator, for small captures)")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 comparison path")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="timed e2e steps (0 = --steps: the same window)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-iters", type=int, default=8)
     return ap.parse_args()
-
-
-def recorded_traffic(w):
-    """DRAM bytes of one assignment launch from a committed ncu capture, if the
-    kernel source is unchanged since the capture (else None)."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", f"assign_kernel_{w.name}_{w.precision}.json")
-    src = os.path.join(ROOT, "paper_2103_16141_gb300", "csrc", "assign.cu")
-    try:
-        rec = json.load(open(path))
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except Exception:
-        return None, None
-    if rec.get("source_sha256") != sha:
-        return None, None
-    return float(rec["dram_bytes_per_launch"]), rec
 
 
 def load_peaks():
@@ -85,6 +91,21 @@ def load_peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def recorded_traffic(w, prec):
+    """DRAM bytes of one assignment launch from a committed ncu summary, if
+    the kernel source is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", f"assign_kernel_{w.name}_{prec}.json")
+    src = os.path.join(ROOT, "paper_2103_16141_gb300", "csrc", "assign.cu")
+    try:
+        rec = json.load(open(path))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except Exception:
+        return None
+    if rec.get("source_sha256") != sha:
+        return None
+    return rec
 
 
 class ClockSampler:
@@ -196,57 +217,71 @@ def replica_throughput(units_local, ms_local, world):
     return sum_over_ranks(float(units_local), world) / (ms / 1e3), ms
 
 
-def cpu_baseline(w, c, ini, iters, icp=1):
-    """The FP64 oracle (OpenMP, all host cores) on a bounded sample of the same
-    workload: the first `iters` Lloyd iterations (assign + update), in the
-    same assignment algorithm."""
-    from oracle import Oracle
-    o = Oracle(c, w.k, ini, icp=icp)
-    t0 = time.perf_counter()
-    done = 0
-    for _ in range(iters):
-        a = o.assign()
-        done += 1
-        if a.r > 1 and a.changed == 0:
-            break
-        o.update()
-    dt = time.perf_counter() - t0
-    cores = Oracle.threads()
-    out = {"value": w.N * done / dt, "unit": "objects/s", "cores": cores, "kind": "oracle",
-           "sample": f"first {done} Lloyd iterations (assign+update) of the same corpus, FP64 oracle, "
-                     f"{dt:.1f} s", "sec_per_iter": dt / done}
-    # one thread, first iteration only (bounded): the per-core figure
-    o1 = Oracle(c, w.k, ini, icp=icp, threads=1)
-    try:
-        t1 = time.perf_counter()
-        o1.assign()
-        o1.update()
-        d1 = time.perf_counter() - t1
-    finally:
-        Oracle(c, w.k, ini, icp=icp, threads=cores)  # restore the thread count
-    t0 = time.perf_counter()
-    o2 = Oracle(c, w.k, ini, icp=icp)
-    o2.assign()
-    o2.update()
-    d2 = time.perf_counter() - t0
-    out["single_thread"] = {"value": w.N / d1, "unit": "objects/s", "sample": "iteration 1, one thread",
-                            "same_sample_all_cores": w.N / d2}
-    return out
-
-
-L2_BYTES = 129 * 2**20  # GB300 L2
-METRIC = "objects/s (Lloyd iterations of SIVF spherical k-means); sec per Lloyd iteration"
-ICP_NAMES = ["ivf", "sivf", "ivf-cbicp", "sivf-relaxed"]
-
-
 def workload_name(w, nnz: int) -> str:
     """The workload as both arms name it in config.workload."""
     return (f"{w.name}: N={w.N} D={w.D} nnz={nnz} k={w.k} zipf={w.zipf_s} "
             f"len=lognormal({w.mu:.3f},{w.sigma}) clip[{w.lo},{w.hi}] seed={w.seed}")
 
 
+def shared_config(w, nnz, args):
+    """The `config` both arms print (identical dicts for the same workload)."""
+    csr_bytes = nnz * 8 + (w.N + 1) * 8
+    return {"workload": workload_name(w, nnz),
+            "window": f"iterations {args.warmup + 1}-{args.warmup + args.steps} of one run from the seeded "
+                      f"centroids (warm-up iterations 1-{args.warmup}); one step = one Lloyd iteration",
+            "l2": (f"inputs larger than L2: every assignment streams the object CSR ({csr_bytes / 1e9:.2f} GB)"
+                   if csr_bytes > L2_BYTES else
+                   f"inputs fit in L2 ({csr_bytes / 1e6:.1f} MB CSR), no flush: a small-case timing")}
+
+
+# ---------------------------------------------------------------- oracle arm
+
+def sampled_reference_state(c, w, ini):
+    """FP64 oracle holding centroids of realistic density for sampled scoring:
+    the means of a seeded balanced labelling (every cluster N/k members)."""
+    from oracle import Oracle
+    o = Oracle(c, w.k, ini, icp=False)
+    rng = np.random.default_rng(w.seed + 77)
+    lab = (rng.permutation(w.N) % w.k).astype(np.int32)
+    o.set_labels(lab)
+    o.update()
+    return o
+
+
+def sampled_oracle_step(o, w, step):
+    """One sampled oracle iteration: REF_SAMPLE seeded objects scored against
+    all k centroids (Algorithm 2 scoring, FP64), then one full update step.
+    Returns (measured seconds, estimated seconds of a whole iteration)."""
+    rng = np.random.default_rng(1000 + step)
+    ids = np.sort(rng.choice(w.N, size=min(REF_SAMPLE, w.N), replace=False)).astype(np.int64)
+    t0 = time.perf_counter()
+    o.score_objects(ids)
+    t1 = time.perf_counter()
+    o.update()
+    t2 = time.perf_counter()
+    return t2 - t0, (t1 - t0) * w.N / len(ids) + (t2 - t1)
+
+
+def full_oracle_iterations(c, w, ini, icp):
+    """Generator of whole oracle Lloyd iterations (assign + update), seconds each."""
+    from oracle import Oracle
+    o = Oracle(c, w.k, ini, icp=icp)
+    while True:
+        t0 = time.perf_counter()
+        a = o.assign()
+        if a.r > 1 and a.changed == 0:  # converged: restart from the seeds
+            o = Oracle(c, w.k, ini, icp=icp)
+            a = o.assign()
+        o.update()
+        yield time.perf_counter() - t0
+
+
+def oracle_is_sampled(w) -> bool:
+    return float(w.N) * w.k > 1e9  # whole iterations only for the small and medium corpora
+
+
 def run_reference(args, w):
-    """Reference arm: the FP64 CPU oracle, each step one Lloyd iteration."""
+    """Reference arm: the FP64 CPU oracle on the same workload and window."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and rank != 0:
@@ -254,31 +289,228 @@ def run_reference(args, w):
     from oracle import Oracle
     c = generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, w.seed)
     ini = init_ids(w.N, w.k, w.init_seed)
-    o = Oracle(c, w.k, ini, icp=args.icp)
-
-    def step():
-        a = o.assign()
-        if a.r > 1 and a.changed == 0:
-            o.set_labels(o.labels())
-        o.update()
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
-    value = w.N * args.steps / dt
+    if oracle_is_sampled(w):
+        o = sampled_reference_state(c, w, ini)
+        for s in range(args.warmup):
+            sampled_oracle_step(o, w, s)
+        meas, est = 0.0, 0.0
+        for s in range(args.steps):
+            m, e = sampled_oracle_step(o, w, args.warmup + s)
+            meas += m
+            est += e
+        value = w.N * args.steps / est
+        ms_step = meas / args.steps * 1e3
+        sample = (f"per step: {REF_SAMPLE} seeded objects scored in FP64 against all k centroids (unfiltered, "
+                  f"Algorithm 2 scoring; time scaled by N/{REF_SAMPLE}) plus one whole update step; the "
+                  f"centroids are the means of a seeded balanced labelling (N/k members each), since the oracle "
+                  f"cannot run whole iterations of this corpus; ms_per_step is the measured sample time, value "
+                  f"the estimated whole iterations: {est / args.steps:.1f} s each")
+    else:
+        it = full_oracle_iterations(c, w, ini, args.icp)
+        for _ in range(args.warmup):
+            next(it)
+        t = sum(next(it) for _ in range(args.steps))
+        value = w.N * args.steps / t
+        ms_step = t / args.steps * 1e3
+        sample = f"iterations {args.warmup + 1}..{args.warmup + args.steps} of the corpus, whole Lloyd iterations"
     line = {"metric": METRIC, "value": value, "unit": "objects/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference",
-            "config": {"workload": workload_name(w, c.nnz), "icp": ICP_NAMES[args.icp], "max_iter": w.max_iter,
-                       "iters_per_step": 1},
+            "impl": "reference", "config": shared_config(w, c.nnz, args),
             "cpu_baseline": {"value": value, "unit": "objects/s", "cores": Oracle.threads(), "kind": "oracle",
-                             "sample": f"iterations {args.warmup + 1}..{args.warmup + args.steps} of the corpus"},
+                             "sample": sample},
             "e2e": {"value": value, "unit": "objects/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(w, c, ini, icp):
+    """The FP64 oracle (OpenMP, all host cores) on a bounded sample of the same
+    workload (about 10-30 s of CPU work)."""
+    from oracle import Oracle
+    cores = Oracle.threads()
+    if oracle_is_sampled(w):
+        o = sampled_reference_state(c, w, ini)
+        meas = est = 0.0
+        steps = 2
+        for s in range(steps):
+            m, e = sampled_oracle_step(o, w, s)
+            meas += m
+            est += e
+        return {"value": w.N * steps / est, "unit": "objects/s", "cores": cores, "kind": "oracle",
+                "sample": f"{steps} sampled iterations: {REF_SAMPLE} seeded objects scored in FP64 against all k "
+                          f"centroids (scaled by N/{REF_SAMPLE}) plus one whole update step each, {meas:.1f} s "
+                          f"measured", "sec_per_iter": est / steps}
+    it = full_oracle_iterations(c, w, ini, icp)
+    t, done = 0.0, 0
+    while done < 8 and t < 20.0:
+        t += next(it)
+        done += 1
+    return {"value": w.N * done / t, "unit": "objects/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {done} Lloyd iterations (assign+update) of the same corpus, FP64 oracle, {t:.1f} s",
+            "sec_per_iter": t / done}
+
+
+# ---------------------------------------------------------------- CUDA arm
+
+def measure_peaks(dev, stream):
+    """Streaming-read bandwidth measured here with CUDA events: a 64 MB buffer
+    (L2-resident) and a 4 GB one (HBM)."""
+    import torch
+    from paper_2103_16141_gb300 import sivf as S
+    out = {}
+    for name, nbytes, passes in (("l2", 64 << 20, 400), ("hbm", 4 << 30, 5)):
+        buf = torch.zeros(nbytes // 4, dtype=torch.int32, device=dev)
+        best = 0.0
+        for _ in range(3):
+            gbs, _ = S.sivf_measure_read_bandwidth(buf.data_ptr(), nbytes, passes, stream.cuda_stream)
+            best = max(best, gbs)
+        out[name] = best
+        del buf
+    torch.cuda.empty_cache()
+    return out
+
+
+class Path:
+    """One clustering run stepped one Lloyd iteration at a time."""
+
+    def __init__(self, c, csr, w, ini, precision, args):
+        from paper_2103_16141_gb300 import SIVF
+        self.w, self.ini = w, ini
+        rp, ix, vl = csr
+        self.g = SIVF(rp, ix, vl, c.D, w.k, ini, precision=precision, icp=args.icp, threads=args.threads,
+                      ctas_per_sm=args.ctas_per_sm, autotune=bool(args.autotune),
+                      dense_max_bytes=int(args.dense_max_mb * 2**20) if args.dense_max_mb >= 0 else -1,
+                      dense_min_fraction=args.dense_min_fraction, update_mode=args.update_mode)
+        self.converged = False
+        self.resets = 0
+
+    def step(self):
+        """One Lloyd iteration; returns the assignment's counters plus the
+        update's device time. A converged run restarts from the seeds."""
+        g = self.g
+        if self.converged:
+            g.reseed(self.ini)
+            self.converged = False
+            self.resets += 1
+        n = g.assign()
+        st = g.stats()
+        rec = dict(st)
+        if st["iter"] > 1 and n == 0:
+            self.converged = True
+            rec["ms_update"] = 0.0
+        else:
+            g.update()
+            su = g.stats()
+            rec["ms_update"] = su["ms_update"]
+            rec["centroid_nnz"] = su["centroid_nnz"]
+        return rec
+
+    def close(self):
+        self.g.close()
+
+
+def timed_window(path, args, stream, world, sampler=None):
+    import torch
+    for _ in range(args.warmup):
+        path.step()
+    if sampler:
+        sampler.start()
+    barrier_and_sync(world)
+    l0 = path.g.stats()["launches"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    per = [path.step() for _ in range(args.steps)]
+    ev1.record(stream)
+    barrier_and_sync(world)
+    clocks = sampler.stop() if sampler else None
+    launches = path.g.stats()["launches"] - l0 if path.resets == 0 else None
+    return ev0.elapsed_time(ev1), per, launches, clocks
+
+
+def roofline(per, w, nnz, prec, peaks, hbm_peak, sparse_file_bytes, dense_bytes):
+    """Roofline of the assignment kernel over a window of iterations.
+
+    Algorithmic bytes per launch: object CSR (nnz * 8 + (N + 1) * 8), per-object
+    state (N * 16: labels old/new, own score read/write) and lambda (k), the
+    sparse postings visited * bytes per posting and the dense-row entries read
+    * bytes per entry. Each part is assigned to the memory that serves it: the
+    CSR and the per-object state stream from HBM; postings and dense rows come
+    from L2 when their structure fits in L2, else from HBM. The bound is the
+    side that serves most of the bytes, and frac is achieved / that side's
+    measured peak."""
+    b_post = (B_POST16 if w.k <= 65536 else B_POST32)[prec]
+    b_dense = B_DENSE[prec]
+    fixed = nnz * 8 + (w.N + 1) * 8 + w.N * 16 + w.k
+    ms = sum(p["ms_assign"] for p in per)
+    sparse = sum(p["postings"] - p.get("dense_postings", 0) for p in per) * b_post
+    dense = sum(p.get("dense_entries", 0) for p in per) * b_dense
+    alg = fixed * len(per) + sparse + dense
+    from_l2 = (sparse if sparse_file_bytes <= L2_BYTES else 0) + (dense if dense_bytes <= L2_BYTES else 0)
+    bound = "l2" if from_l2 > alg / 2 else "hbm"
+    achieved = alg / (ms / 1e3) / 1e9
+    peak = peaks["l2"] if bound == "l2" else hbm_peak
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": ("measured here: streaming reads of a 64 MB L2-resident buffer (CUDA events)"
+                            if bound == "l2" else "MEASURED_PEAKS.json hbm_gbs (measured)"),
+            "hbm_frac": achieved / hbm_peak, "l2_frac": achieved / peaks["l2"],
+            "kernel": "assign_kernel", "bytes_per_launch": alg / len(per),
+            "bytes_model": f"nnz*8 + (N+1)*8 + N*16 + k + postings read one by one*{b_post} B + dense-row "
+                           f"entries read*{b_dense} B (no cache credit)",
+            "bytes_from_l2_structures": from_l2 / max(alg, 1),
+            "ms_assign_per_iter": ms / len(per),
+            "ms_update_per_iter": sum(p["ms_update"] for p in per) / len(per),
+            "postings_per_s": sum(p["postings"] for p in per) / (ms / 1e3),
+            "dense_entries_per_s": sum(p.get("dense_entries", 0) for p in per) / (ms / 1e3),
+            "simcalc_ratio": sum(p["simcalc"] for p in per) / (float(w.N) * w.k * len(per))}
+
+
+def file_bytes(g, prec, k):
+    """Bytes of the sparse scan copy (at most every posting of the file) and of
+    the dense head rows of the current inverted file (library counters)."""
+    st = g.stats()
+    b_post = (B_POST16 if k <= 65536 else B_POST32)[prec]
+    return st["centroid_nnz"] * b_post, st["dense_row_entries"] * B_DENSE[prec]
+
+
+def trajectory(per):
+    return [(int(p["changed"]), int(p["postings"]), int(p.get("dense_entries", 0)), int(p["filtered"]),
+             int(p["n_moving"])) for p in per]
+
+
+def run_e2e(c, csr, w, ini, prec, args, stream, world):
+    """The same window through the C ABI with host buffers: every timed step
+    copies the CSR from pinned host memory into the device buffers the context
+    reads, runs one Lloyd iteration and reads the labels back."""
+    import torch
+    from paper_2103_16141_gb300 import sivf as S
+    rp_d, ix_d, vl_d = csr
+    rp_h = torch.from_numpy(c.row_ptr).pin_memory()
+    ix_h = torch.from_numpy(c.idx).pin_memory()
+    vl_h = torch.from_numpy(c.val).pin_memory()
+    lab_h = torch.empty(w.N, dtype=torch.int32).pin_memory()
+    path = Path(c, csr, w, ini, prec, args)
+    try:
+        for _ in range(args.warmup):
+            path.step()
+        E = args.e2e_steps if args.e2e_steps > 0 else args.steps
+        barrier_and_sync(world)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for _ in range(E):
+                rp_d.copy_(rp_h, non_blocking=True)
+                ix_d.copy_(ix_h, non_blocking=True)
+                vl_d.copy_(vl_h, non_blocking=True)
+                path.step()
+                S.sivf_get_labels(path.g.ctx, lab_h.data_ptr(), False)
+        barrier_and_sync(world)
+        dt = max_over_ranks(time.perf_counter() - t0, world)
+    finally:
+        path.close()
+    h2d = rp_h.numel() * 8 + ix_h.numel() * 4 + vl_h.numel() * 4
+    return {"value": sum_over_ranks(float(w.N * E), world) / dt, "unit": "objects/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": w.N * 4, "steps": E,
+            "window": f"iterations {args.warmup + 1}-{args.warmup + E}, a separate run from the same seeds"
+                      + (" (the timed window)" if E == args.steps else "")}
 
 
 def run_batched(args):
@@ -348,175 +580,97 @@ def main():
         run_batched(args)
         return
     w = CONFIGS[args.config]
-    if args.precision:
-        w = w.scaled(precision=args.precision)
-    if args.max_iter:
-        w = w.scaled(max_iter=args.max_iter)
+    prec = args.precision or w.precision
     if args.impl == "reference":
         run_reference(args, w)
         return
 
     import torch
-    from paper_2103_16141_gb300 import SIVF, sivf as S
+    from paper_2103_16141_gb300 import sivf as S
 
     world, rank, local = dist_setup(args.gpus)
     S.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
     # each rank is an independent replica of the workload (the path needs no exchange)
     c = generate(w.N, w.D, w.zipf_s, w.mu, w.sigma, w.lo, w.hi, w.seed)
     ini = init_ids(w.N, w.k, w.init_seed)
-    dev = torch.device("cuda", torch.cuda.current_device())
-    g = SIVF(c.row_ptr, c.idx, c.val, c.D, w.k, ini, precision=w.precision, icp=args.icp,
-             threads=args.threads, ctas_per_sm=args.ctas_per_sm, use_graph=bool(args.graph),
-             autotune=bool(args.autotune))
-    stream = torch.cuda.current_stream()
+    csr = (torch.from_numpy(c.row_ptr).to(dev), torch.from_numpy(c.idx).to(dev), torch.from_numpy(c.val).to(dev))
+    hbm_peak, _ = load_peaks()
+    peaks = measure_peaks(dev, stream)
 
-    def one_run_stepped():
-        """Host-stepped run: per-iteration counters and per-launch device times."""
-        g.reseed(ini)
-        iters = 0
-        per = []
-        for _ in range(w.max_iter):
-            n = g.assign()
-            iters += 1
-            st = g.stats()
-            per.append(st)
-            if st["iter"] > 1 and n == 0:
-                break
-            g.update()
-            per[-1] = {**st, "ms_update": g.stats()["ms_update"], "centroid_nnz": g.stats()["centroid_nnz"]}
-        per[-1]["launches_run"] = g.stats()["launches"]  # reseed resets the count
-        return iters, per
-
-    def one_run_graph():
-        g.reseed(ini)
-        iters, _ = g.run(w.max_iter)
-        return iters, [{"launches_run": g.stats()["launches"]}]
-
-    one_run = one_run_graph if args.graph else one_run_stepped
-
-    for _ in range(args.warmup):
-        one_run()
-
+    # the path of record
+    path = Path(c, csr, w, ini, prec, args)
     sampler = ClockSampler(local)
-    sampler.start()
-    barrier_and_sync(world)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    tot_iters, all_per = 0, []
-    for _ in range(args.steps):
-        it, per = one_run()
-        tot_iters += it
-        all_per.extend(per)
-    ev1.record(stream)
-    barrier_and_sync(world)
-    clocks = sampler.stop()
-    launches = sum(p["launches_run"] for p in all_per if "launches_run" in p)
-    value, ms = replica_throughput(w.N * tot_iters, ev0.elapsed_time(ev1), world)
+    ms, per, launches, clocks = timed_window(path, args, stream, world, sampler)
+    sparse_b, dense_b = file_bytes(path.g, prec, w.k)
+    st_end = path.g.stats()
+    lab_end = path.g.labels()
+    path.close()
+    value, ms_max = replica_throughput(w.N * args.steps, ms, world)
+    roof = roofline(per, w, c.nnz, prec, peaks, hbm_peak, sparse_b, dense_b)
+    trec = recorded_traffic(w, prec)
+    roof["traffic"] = trec["dram_bytes_per_launch"] if trec else None
+    roof["traffic_launch"] = trec.get("launch") if trec else None
 
-    # roofline of the dominant kernel (the assignment scan), from the library's
-    # per-launch event timings: over the timed region when steps are launched
-    # from the host, else over one host-stepped run of the same workload
-    kernel_times_from = "timed region"
-    if args.graph:
-        _, all_per = one_run_stepped()
-        kernel_times_from = "one host-stepped run of the same workload (graph replay hides per-launch times)"
-    hbm_peak, peak_src = load_peaks()
-    b_post = (B_POST16 if w.k <= 65536 else B_POST32)[w.precision]
-    fixed = c.nnz * 8 + (w.N + 1) * 8 + w.N * 16 + w.k
-    alg_bytes = sum(fixed + p["postings"] * b_post for p in all_per)
-    # compulsory bytes: every posting of the scanned file read once (the file
-    # of iteration r is built by update r-1; the first one holds the seed rows)
-    seed_nnz = int(sum(c.row_ptr[i + 1] - c.row_ptr[i] for i in ini))
-    if_nnz = [seed_nnz] + [p.get("centroid_nnz", 0) for p in all_per[:-1]]
-    min_bytes = sum(fixed + n * b_post for n in if_nnz)
-    ms_assign = sum(p["ms_assign"] for p in all_per)
-    ms_update = sum(p.get("ms_update", 0.0) for p in all_per)
-    stepped_iters = len(all_per)
-    achieved = alg_bytes / (ms_assign / 1e3) / 1e9 if ms_assign > 0 else 0.0
-    postings = sum(p["postings"] for p in all_per)
-    simcalc = sum(p["simcalc"] for p in all_per)
-    iters_per_step = tot_iters / args.steps
-    traffic, trec = recorded_traffic(w)
+    # the FP32 path on the same window
+    vs_fp32 = None
+    if not args.no_fp32 and prec != "fp32":
+        p32 = Path(c, csr, w, ini, "fp32", args)
+        ms32, per32, _, _ = timed_window(p32, args, stream, world)
+        sb32, db32 = file_bytes(p32.g, "fp32", w.k)
+        lab32 = p32.g.labels()
+        p32.close()
+        _, ms32_max = replica_throughput(w.N * args.steps, ms32, world)
+        same = trajectory(per) == trajectory(per32) and bool(np.array_equal(lab_end, lab32))
+        vs_fp32 = {"sec_per_iter": ms_max / 1e3 / args.steps, "fp32_sec_per_iter": ms32_max / 1e3 / args.steps,
+                   "speedup": ms32_max / ms_max, "precision": prec,
+                   "fp32_roofline": roofline(per32, w, c.nnz, "fp32", peaks, hbm_peak, sb32, db32),
+                   "labels_identical_every_iteration": same,
+                   "equal_accuracy": "both paths re-score every object whose top-2 margin lies inside their "
+                                     "derived error bound exactly (FP64 from the FP32 master centroids), so both "
+                                     "give the argmax of the exact scores: the per-iteration changed/posting/"
+                                     "filtered/moving counts and the final labels are compared"}
 
-    # end to end: host corpus in pinned memory -> device, init, run, labels back
-    e2e = None
-    if not args.no_e2e:
-        # the C ABI copies the pinned host CSR itself (inputs_on_host)
-        rp = torch.from_numpy(c.row_ptr).pin_memory()
-        ix = torch.from_numpy(c.idx).pin_memory()
-        vl = torch.from_numpy(c.val).pin_memory()
-        lab_host = torch.empty(w.N, dtype=torch.int32).pin_memory()
-        h2d = rp.numel() * 8 + ix.numel() * 4 + vl.numel() * 4
-        d2h = w.N * 4
-        barrier_and_sync(world)
-        t0 = time.perf_counter()
-        e_iters = 0
-        E = max(1, min(args.steps, 3))
-        for _ in range(E):
-            ge = SIVF(rp, ix, vl, c.D, w.k, ini, precision=w.precision, icp=args.icp,
-                      threads=args.threads, ctas_per_sm=args.ctas_per_sm, use_graph=bool(args.graph),
-                      autotune=bool(args.autotune), inputs_on_host=True)
-            it, _ = ge.run(w.max_iter)
-            e_iters += it
-            S.sivf_get_labels(ge.ctx, lab_host.data_ptr(), False)
-            ge.close()
-        barrier_and_sync(world)
-        dt = max_over_ranks(time.perf_counter() - t0, world)
-        e2e = {"value": sum_over_ranks(float(w.N * e_iters), world) / dt, "unit": "objects/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": E}
-
+    e2e = None if args.no_e2e else run_e2e(c, csr, w, ini, prec, args, stream, world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, c, ini, args.cpu_sample_iters, args.icp)
+        cpu = cpu_baseline(w, c, ini, args.icp)
 
     if rank == 0:
-        csr_bytes = c.nnz * 8 + (w.N + 1) * 8
         line = {
             "metric": METRIC,
             "value": value, "unit": "objects/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if w.precision == "fp32" else f"{w.precision}-postings/f32-products/fixed-point-sum",
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == "fp32" else f"{prec}-postings/f32-products/fixed-point-sum",
             "data": "synthetic",
-            "config": {"workload": workload_name(w, c.nnz),
-                       "precision": w.precision, "icp": ICP_NAMES[args.icp], "max_iter": w.max_iter,
-                       "iters_per_step": iters_per_step, "sec_per_iter": ms / 1e3 / tot_iters,
-                       "l2": (f"inputs larger than L2: every assignment streams the object CSR "
-                              f"({csr_bytes / 1e9:.2f} GB); the inverted file is reused from L2 within a launch"
-                              if csr_bytes > L2_BYTES else
-                              f"inputs fit in L2 ({csr_bytes / 1e6:.1f} MB CSR), no flush: a small-case timing, "
-                              f"not the workload of record"),
-                       "parallelism": "replicas" if world > 1 else "single GPU",
-                       "cuda_graph": bool(args.graph), "autotune": bool(args.autotune),
-                       "assign_threads": g.stats()["assign_threads"],
-                       "score_buffer": "global" if g.stats()["assign_global"] else "shared"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": traffic,
-                         "traffic_launch": trec.get("launch") if trec else None,
-                         "peak_source": peak_src, "kernel": "assign_kernel",
-                         "bytes_model": f"nnz*8 + (N+1)*8 + postings*b_post + N*16 + k, b_post = {b_post} B "
-                                        f"(no cache credit)",
-                         "note": "posting bytes are served by L2, not HBM (traffic = ncu DRAM bytes of one "
-                                 "launch); frac > 1 means on-chip reuse, see profiles/",
-                         "compulsory_frac": min_bytes / (ms_assign / 1e3) / 1e9 / hbm_peak if ms_assign > 0 else None,
-                         "ncu_dram_gbs": (traffic / trec["ncu_duration_s"] / 1e9) if trec else None,
-                         "postings_per_s": postings / (ms_assign / 1e3) if ms_assign > 0 else None,
-                         "simcalc_ratio": simcalc / (float(w.N) * w.k * stepped_iters),
-                         "ms_assign_per_iter": ms_assign / stepped_iters, "ms_update_per_iter": ms_update / stepped_iters,
-                         "kernel_times_from": kernel_times_from},
-            "per_iteration": {"postings": [int(p["postings"]) for p in all_per[:60]],
-                              "filtered": [int(p["filtered"]) for p in all_per[:60]],
-                              "rescored": [int(p["rescored"]) for p in all_per[:60]],
-                              "ms_assign": [round(p["ms_assign"], 3) for p in all_per[:60]],
-                              "ms_update": [round(p.get("ms_update", 0.0), 3) for p in all_per[:60]]},
-            "gpu_launches": int(launches),
+            "config": shared_config(w, c.nnz, args),
+            "details": {"precision": prec, "icp": ICP_NAMES[args.icp], "sec_per_iter": ms_max / 1e3 / args.steps,
+                        "parallelism": "replicas" if world > 1 else "single GPU",
+                        "autotune": bool(args.autotune), "assign_threads": st_end["assign_threads"],
+                        "score_buffer": "global" if st_end["assign_global"] else "shared",
+                        "restarts_in_window": path.resets, "measured_peaks_gbs": peaks,
+                        "dense_terms": st_end["dense_terms"], "dense_row_bytes": dense_b},
+            "roofline": roof,
+            "per_iteration": {"iteration": [int(p["iter"]) for p in per],
+                              "postings": [int(p["postings"]) for p in per],
+                              "dense_postings": [int(p.get("dense_postings", 0)) for p in per],
+                              "dense_entries": [int(p.get("dense_entries", 0)) for p in per],
+                              "filtered": [int(p["filtered"]) for p in per],
+                              "rescored": [int(p["rescored"]) for p in per],
+                              "changed": [int(p["changed"]) for p in per],
+                              "ms_assign": [round(p["ms_assign"], 3) for p in per],
+                              "ms_update": [round(p["ms_update"], 3) for p in per]},
+            "gpu_launches": int(launches) if launches is not None else None,
             "clocks": clocks,
         }
+        if vs_fp32:
+            line["vs_fp32"] = vs_fp32
         if e2e:
             line["e2e"] = e2e
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
-    g.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

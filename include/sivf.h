@@ -97,6 +97,27 @@ typedef struct {
                             sivf_destroy, and the host arrays may be released once
                             sivf_init returns. 0: DEVICE memory, borrowed. sivf_batch_init
                             rejects 1 (its descriptors are DEVICE). */
+    int checked;         /* 1: the assignment step checks every object's row offsets
+                            (0 <= row_ptr[i] <= row_ptr[i+1] <= nnz) and terms (in
+                            [0, D)) before using them, as the borrowed CSR may have
+                            changed since sivf_init validated it. A failed check reads
+                            nothing through the bad value, records a device-side status
+                            word, and the assignment then returns SIVF_ERR_STATE with
+                            the context latched. Checked contexts step every iteration
+                            from the host (no CUDA-graph loop), so no update runs on
+                            unchecked data. 0: the CSR is trusted after validation. */
+    int64_t dense_max_bytes;  /* device memory for dense head-term rows. The posting
+                            lists that hold a large share of their instance's k
+                            centroids are stored as dense rows (one value per cluster,
+                            0 where a cluster lacks the term, in scan order: moving
+                            clusters first) and read with vector loads into FP32
+                            registers instead of per-posting score atomics. Rows take
+                            k x 2 bytes (BF16/FP16) or k x 4 bytes (FP32) each.
+                            0 = automatic (96 MB, below the L2 size), < 0 = none */
+    float dense_min_fraction; /* a list becomes a dense row when it holds at least this
+                            fraction of its instance's k (the threshold rises while the
+                            rows would exceed dense_max_bytes); 0 = automatic (0.25).
+                            Must be in [0, 1]. IVF-CBICP (icp = 2) uses no dense rows */
 } sivf_config;
 
 /* Counters of the most recent assignment / update (host copy). */
@@ -107,7 +128,8 @@ typedef struct {
     int64_t n_moving_prev;   /* clusters with lambda^[r-1] = 0 (candidates of a filtered object) */
     int64_t filtered;        /* objects that took the filtered (front-only) branch */
     int64_t simcalc;         /* similarity calculations: k per unfiltered, n_moving_prev per filtered object */
-    int64_t postings;        /* postings visited by the scan */
+    int64_t postings;        /* postings visited by the scan (the method's count: the
+                                scanned segments' lengths, whichever layout held them) */
     int64_t rescored;        /* objects re-scored in FP64 (top-2 margin inside the error bound) */
     int64_t rescore_cands;   /* candidate centroids re-scored in FP64 */
     int64_t centroid_nnz;    /* non-zeros of the centroid set M^[r] after the last update */
@@ -126,6 +148,11 @@ typedef struct {
     int32_t assign_threads;  /* threads per CTA of the assignment kernel in use */
     int32_t assign_global;   /* 1 if its score vectors live in global memory */
     int32_t update_dense;    /* 1 if the update step sums into the dense accumulator */
+    int64_t dense_entries;   /* dense-row entries read by the last assignment */
+    int64_t dense_postings;  /* of `postings`, those of terms read from dense rows (the
+                                rest were read one posting at a time) */
+    int64_t dense_terms;     /* terms with a dense row in the current inverted file */
+    int64_t dense_row_entries; /* entries of those rows (padded to multiples of 8) */
 } sivf_stats;
 
 typedef struct sivf_ctx sivf_ctx; /* opaque, library-owned */
@@ -310,19 +337,27 @@ void sivf_destroy(sivf_ctx *ctx);
  * each part, with their values. It allocates nothing: its scratch is a
  * file-scope static device array of SIVF_NOALLOC_SCRATCH_BYTES that every GPU
  * loading the library holds until the process exits.
- *   k, D      : clusters and terms; 1 <= D <= SIVF_NOALLOC_MAX_TERMS.
+ *   k, D      : clusters and terms; 1 <= k <= SIVF_NOALLOC_MAX_CLUSTERS,
+ *               1 <= D <= SIVF_NOALLOC_MAX_TERMS.
  *   n_entries : HOST, total centroid non-zeros = coff[k];
  *               0 <= n_entries <= SIVF_NOALLOC_MAX_ENTRIES.
  *   coff      : DEVICE int64[k+1], cterm : DEVICE int32[n_entries] (ascending
- *               terms in each row), cval : DEVICE float[n_entries] — the
- *               cluster-major centroids (sivf_get_centroids layout).
+ *               terms in each row, each in [0, D)), cval : DEVICE
+ *               float[n_entries] — the cluster-major centroids
+ *               (sivf_get_centroids layout).
  *   lam       : DEVICE uint8[k], 1 = invariant.
  *   if_off    : DEVICE int64[D+1] out, if_mf0 : DEVICE int32[D] out (front
  *               length), if_cid : DEVICE int32[n_entries] out,
  *               if_u : DEVICE float[n_entries] out. Caller-owned.
- *   stream    : cudaStream_t; all work is ordered on it (nothing synchronises).
+ *   stream    : cudaStream_t; all work is ordered on it. The call waits for
+ *               the stream once, at its end, to read the result of its
+ *               device-side checks.
  * Errors: SIVF_ERR_INVALID_ARG, with nothing launched, when a size is beyond
- * the limits above or a pointer is NULL; SIVF_ERR_CUDA on a CUDA failure.
+ * the limits above or a pointer is NULL; SIVF_ERR_INVALID_ARG after the
+ * device-side checks when coff is not a valid offset array (coff[0] = 0,
+ * non-decreasing, coff[k] = n_entries) or a term lies outside [0, D): the
+ * outputs are then unspecified, and nothing outside the arrays above and the
+ * scratch is touched; SIVF_ERR_CUDA on a CUDA failure.
  * The first call on a device looks up the scratch array's device address
  * (once per device, with that device current); make that first call before
  * any stream capture begins. Every call reuses the same array and clears what
@@ -330,11 +365,31 @@ void sivf_destroy(sivf_ctx *ctx);
  */
 #define SIVF_NOALLOC_MAX_ENTRIES (1 << 20)
 #define SIVF_NOALLOC_MAX_TERMS (1 << 18)
+#define SIVF_NOALLOC_MAX_CLUSTERS (1 << 20)
 #define SIVF_NOALLOC_SCRATCH_BYTES (26u << 20)
 sivf_status sivf_build_inverted_file_noalloc(int32_t k, int32_t D, int64_t n_entries, const int64_t *coff,
                                              const int32_t *cterm, const float *cval, const uint8_t *lam,
                                              int64_t *if_off, int32_t *if_mf0, int32_t *if_cid, float *if_u,
                                              void *stream);
+
+/*
+ * sivf_measure_read_bandwidth — streaming-read bandwidth of a device buffer,
+ * measured with CUDA events on `stream`: the denominator of the assignment
+ * scan's roofline when its posting stream is served by L2. The paper has no
+ * counterpart (it measures on CPUs).
+ *   buf     : DEVICE, 16-byte aligned, `bytes` readable bytes (only read).
+ *   bytes   : >= 16; whole 16-byte vectors are read. A buffer that fits in L2
+ *             (129 MB on GB300) measures L2 -> SM delivery, a larger one HBM.
+ *   passes  : >= 1 timed passes over the buffer, after one untimed warm pass.
+ *             Loads bypass L1 (ld.global.cg), and every SM reads a different
+ *             slice in consecutive passes.
+ *   gbs_out : HOST out, bytes read per second / 1e9; ms_out: HOST out (may be
+ *             NULL), the timed duration.
+ * Synchronises the stream. Errors: SIVF_ERR_INVALID_ARG (NULL, misaligned or
+ * too small), SIVF_ERR_CUDA.
+ */
+sivf_status sivf_measure_read_bandwidth(const void *buf, int64_t bytes, int32_t passes, void *stream,
+                                        double *gbs_out, double *ms_out);
 
 #ifdef __cplusplus
 }

@@ -52,7 +52,8 @@ void free_all(sivf_ctx *c) {
                     c->cval[0], c->cval[1], c->cclu, c->if_off, c->if_mf0, c->if_cid, c->if_val, c->sc_off, c->sc_id16, c->sc_id32, c->sc_val, c->sc_pack, c->sc_lp,
                     c->ctr, c->obj_dev, c->ws.base, c->inst_obj, c->inst_k, c->mov_beg, c->clu_koff,
                     c->inst_changed, c->own_row_ptr, c->own_idx, c->own_val, c->clu_doff,
-                    c->loop_dev, c->done_dev, c->objf_dev, c->grho, c->acc, c->acc_off, c->acc_lab};
+                    c->loop_dev, c->done_dev, c->objf_dev, c->grho, c->acc, c->acc_off, c->acc_lab,
+                    c->clu_pos, c->pos_clu, c->dense_row, c->dense_val, c->inst_d, c->dense_thr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     destroy_loop_graph(c);
@@ -67,6 +68,16 @@ sivf_status check_usable(sivf_ctx *c) {
     if (!c) return SIVF_ERR_INVALID_ARG;
     if (c->latched) return SIVF_ERR_STATE;
     return SIVF_OK;
+}
+
+// Dense-row counters of the inverted file built by sivf_init / sivf_reseed
+// (later builds report them through the update step's counters).
+cudaError_t read_file_counters(sivf_ctx *c) {
+    SIVF_CUDA_TRY(cudaMemcpyAsync(c->ctr_host, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->stream));
+    SIVF_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->dense_terms_h = c->ctr_host->dense_terms;
+    c->dense_used_h = c->ctr_host->dense_used * 8;
+    return cudaSuccess;
 }
 
 void pick_assign_config(sivf_ctx *c) {
@@ -227,6 +238,20 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
         INIT_CUDA(dmalloc(c, &c->sc_id32, caps), "alloc");
         INIT_CUDA(dmalloc(c, &c->sc_lp, caps), "alloc");
     }
+    // scan order and dense head rows
+    INIT_CUDA(dmalloc(c, &c->clu_pos, k), "alloc");
+    INIT_CUDA(dmalloc(c, &c->pos_clu, k), "alloc");
+    INIT_CUDA(dmalloc(c, &c->dense_row, D), "alloc");
+    INIT_CUDA(dmalloc(c, &c->inst_d, (size_t)ni + 1), "alloc");
+    INIT_CUDA(dmalloc(c, &c->dense_thr, 1), "alloc");
+    {
+        const int64_t esize = c->cfg.prec == SIVF_FP32 ? 4 : 2;
+        const int64_t bytes = c->cfg.dense_max_bytes == 0 ? (int64_t)96 << 20 : c->cfg.dense_max_bytes;
+        c->cap_dense = (c->cfg.icp == 2 || bytes < 0) ? 0 : (bytes / esize) & ~(int64_t)7;
+        c->dense_frac = c->cfg.dense_min_fraction > 0.f ? c->cfg.dense_min_fraction : 0.25f;
+        if (c->cap_dense > 0) INIT_CUDA(dmalloc(c, reinterpret_cast<uint16_t **>(&c->dense_val),
+                                                (size_t)(c->cap_dense * esize / 2)), "alloc dense rows");
+    }
     INIT_CUDA(dmalloc(c, &c->ctr, 1), "alloc");
     INIT_CUDA(dmalloc(c, &c->obj_dev, 2 * (size_t)ni), "alloc");
     INIT_CUDA(cudaMallocHost(reinterpret_cast<void **>(&c->ctr_host), sizeof(DevCounters)), "alloc host");
@@ -286,7 +311,9 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
         // term, rank, value, sorted value, 64-bit key, piece sum, unique term
         // and sum (60 B)
         size_t phase1 = 4 * (size_t)N * 4 + 2 * n8 + 14 * k8 + (c->dense ? 0 : 64 * ((size_t)nnz + 1)) + 32 * 4096;
-        size_t phase2 = 16 * ((size_t)capc + 1) + 32 * ((size_t)D + 1) + 16 * 4096;
+        // u5: sort arrays (16 B x entries), per-term counts, lengths, dense widths
+        // and offsets (40 B x terms), the dense-length histogram
+        size_t phase2 = 16 * ((size_t)capc + 1) + 48 * ((size_t)D + 1) + 16 * 4096;
         size_t ws = phase1 > phase2 ? phase1 : phase2;
         size_t maxn = (size_t)(capc > N ? capc : N);
         ws += (maxn / 4096 + 2) * 1024 * 4 + (maxn / 2048 + 2) * 16 + 64 * 256 + (1 << 20);
@@ -312,6 +339,8 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
                                   c->stream), "copy");
         INIT_CUDA(cudaMemcpyAsync(c->inst_k, inst_k.data(), sizeof(int32_t) * (ni + 1), cudaMemcpyHostToDevice,
                                   c->stream), "copy");
+        INIT_CUDA(cudaMemcpyAsync(c->inst_d, inst_d.data(), sizeof(int32_t) * (ni + 1), cudaMemcpyHostToDevice,
+                                  c->stream), "copy");
         INIT_CUDA(cudaMemcpyAsync(c->clu_koff, koff.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, c->stream),
                   "copy");
         INIT_CUDA(cudaStreamSynchronize(c->stream), "sync");
@@ -335,6 +364,7 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
         INIT_CUDA(reseed_dev(c, ids_dev), "seed");
     }
     INIT_CUDA(cudaStreamSynchronize(c->stream), "sync");
+    INIT_CUDA(read_file_counters(c), "counters");
     c->ws.reset();
     c->stats.centroid_nnz = c->c_nnz;
 #undef INIT_CUDA
@@ -377,7 +407,8 @@ sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t
     if (N < 1 || N > 0x7FFFFFFFll || D < 1 || D > (1 << 30) || k < 1 || (int64_t)k > N || !row_ptr || !idx || !val ||
         !init_ids)
         return SIVF_ERR_INVALID_ARG;
-    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16 || cfg->icp < 0 || cfg->icp > 3))
+    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16 || cfg->icp < 0 || cfg->icp > 3 ||
+                !(cfg->dense_min_fraction >= 0.f && cfg->dense_min_fraction <= 1.f)))
         return SIVF_ERR_INVALID_ARG;
     if (!distinct_ids(init_ids, k, N)) return SIVF_ERR_INVALID_ARG;
     if (cfg && cfg->inputs_on_host) {
@@ -420,7 +451,8 @@ sivf_status sivf_batch_init(sivf_ctx **out, const sivf_config *cfg, int32_t n_in
     if (!out) return SIVF_ERR_INVALID_ARG;
     *out = nullptr;
     if (n_inst < 1 || n_inst > 65536 || !descs) return SIVF_ERR_INVALID_ARG;
-    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16 || cfg->inputs_on_host || cfg->icp < 0 || cfg->icp > 3))
+    if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16 || cfg->inputs_on_host || cfg->icp < 0 || cfg->icp > 3 ||
+                !(cfg->dense_min_fraction >= 0.f && cfg->dense_min_fraction <= 1.f)))
         return SIVF_ERR_INVALID_ARG;
     std::vector<int64_t> inst_obj(1, 0);
     std::vector<int32_t> inst_k(1, 0), inst_d(1, 0);
@@ -520,9 +552,14 @@ sivf_status sivf_reseed(sivf_ctx *c, const int32_t *init_ids) {
     c->launch_base = g_launches;
     API_CUDA(c, reseed_dev(c, ids_dev), "reseed");
     API_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
+    API_CUDA(c, read_file_counters(c), "counters");
     c->ws.reset();
     c->stats = sivf_stats{};
     c->stats.centroid_nnz = c->c_nnz;
+    // no update has run from these seeds: no objective yet
+    std::fill(c->inst_obj_assign_h.begin(), c->inst_obj_assign_h.end(), 0.0);
+    std::fill(c->inst_obj_update_h.begin(), c->inst_obj_update_h.end(), 0.0);
+    std::fill(c->inst_changed_h.begin(), c->inst_changed_h.end(), 0ull);
     return SIVF_OK;
 }
 
@@ -579,7 +616,8 @@ sivf_status finish_assign(sivf_ctx *c, int64_t *n_changed, float ms) {
     const DevCounters &h = *c->ctr_host;
     if (h.error) {
         c->latched = true;
-        c->err = "device-side check failed in the assignment";
+        c->err = (h.error & 1ull) ? "device-side check failed in the assignment: a row offset of the CSR is out of range"
+                                  : "device-side check failed in the assignment: a term of the CSR is outside [0, D)";
         return SIVF_ERR_STATE;
     }
     for (int32_t m = 0; m < c->n_inst; ++m)
@@ -594,6 +632,8 @@ sivf_status finish_assign(sivf_ctx *c, int64_t *n_changed, float ms) {
     st.postings = (int64_t)h.postings;
     st.rescored = (int64_t)h.rescored;
     st.rescore_cands = (int64_t)h.rescore_cands;
+    st.dense_entries = (int64_t)h.dense_entries;
+    st.dense_postings = (int64_t)h.dense_postings;
     if (ms >= 0.f) st.ms_assign = ms;
     if (n_changed) *n_changed = st.changed;
     return SIVF_OK;
@@ -607,6 +647,8 @@ sivf_status finish_update(sivf_ctx *c, float ms) {
     }
     c->c_nnz = c->ctr_host->c_nnz;
     c->if_nnz = c->c_nnz;
+    c->dense_terms_h = c->ctr_host->dense_terms;
+    c->dense_used_h = c->ctr_host->dense_used * 8;
     c->stats.moved_nnz = c->ctr_host->moved;
     double ja = 0.0, ju = 0.0;
     for (int32_t m = 0; m < c->n_inst; ++m) {
@@ -725,7 +767,7 @@ static sivf_status run_loop(sivf_ctx *c, int32_t max_iter, std::vector<int32_t> 
         for (size_t m = 0; m < ni; ++m) objf[m] = c->inst_obj_update_h[m];
     }
     while (c->iter < max_total && remaining > 0) {
-        if (c->cfg.use_graph && c->iter >= 2 && !c->needs_update) {
+        if (c->cfg.use_graph && !c->cfg.checked && c->iter >= 2 && !c->needs_update) {
             st = graph_loop(c, max_total, done, objf);
             if (st == SIVF_OK) break;
             if (c->latched) return st;  // a real failure; otherwise fall back to host-launched steps
@@ -848,6 +890,8 @@ sivf_status sivf_get_stats(sivf_ctx *c, sivf_stats *out) {
     c->stats.assign_threads = c->assign_threads;
     c->stats.assign_global = c->assign_global;
     c->stats.update_dense = c->dense ? 1 : 0;
+    c->stats.dense_terms = c->dense_terms_h;
+    c->stats.dense_row_entries = c->dense_used_h;
     *out = c->stats;
     return SIVF_OK;
 }

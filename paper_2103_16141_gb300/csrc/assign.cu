@@ -47,6 +47,9 @@ struct AssignParams {
     int64_t N;
     int32_t k;
     int icp;
+    int checked;               // 1: check each object's row offsets and terms before use
+    int32_t D;
+    int64_t nnz;
     const int64_t *row_ptr;
     const int32_t *idx;
     const float *val;
@@ -60,6 +63,11 @@ struct AssignParams {
     const float *sc_val;
     const uint32_t *sc_pack;   // (id << 16) | bf16/fp16 bits, when k <= 65536 and values are 16-bit
     const uint16_t *sc_lp;
+    // scan order and dense head rows
+    const int32_t *clu_pos;    // cluster (global id) -> scan position in its instance
+    const int32_t *pos_clu;    // instance cluster offset + scan position -> local id
+    const int32_t *dense_row;  // [D]: first entry / 8 of the term's dense row, -1 = sparse
+    const void *dense;         // dense rows: u16 (BF16, FP16 x 2^14) or f32
     uint32_t *grho;            // global score vectors, one kmax slab per CTA (global score-buffer variant)
     const int64_t *coff;
     const int32_t *cterm;
@@ -140,10 +148,15 @@ __device__ double exact_score(const AssignParams &P, int64_t rb, int64_t re, int
     return acc;
 }
 
-__device__ __forceinline__ double error_bound(double x, int64_t n, double S, double eps, double eta) {
+// E(x): bound on |rho~ - rho| for a computed score x (see the top of this
+// file); nd = the object's dense terms, whose FP32 chain of nd fused
+// multiply-adds replaces the single rounding of a product (gamma_nd).
+__device__ __forceinline__ double error_bound(double x, int64_t n, int nd, double S, double eps, double eta) {
     const double ur = 5.9604644775390625e-08;  // 2^-24
-    double c = ur * (1.0 + eps) + eps;
-    double a = (double)n * FIX_QUANTUM + (1.0 + ur) * eta * S;
+    const double m = nd > 1 ? (double)nd : 1.0;
+    const double g = m * ur / (1.0 - m * ur);
+    const double c = eps + (1.0 + eps) * g;
+    const double a = 2.0 * (double)n * FIX_QUANTUM + (1.0 + g) * eta * S;
     return (c * x + a) / (1.0 - c) * (1.0 + 1e-12);
 }
 
@@ -174,41 +187,45 @@ __device__ __forceinline__ int block_inclusive_scan_int(int x, int *warp_s, int 
     return warp_s[warp] + inc;
 }
 
-// Inclusive scan of an (x, y) pair over the block (both components at once).
+// Inclusive scan of an int4 over the block (all components at once).
 template <int T>
-__device__ __forceinline__ int2 block_inclusive_scan_int2(int2 v, int2 *warp_s, int2 *total) {
+__device__ __forceinline__ int4 block_inclusive_scan_int4(int4 v, int4 *warp_s, int4 *total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int2 inc = v;
+    int4 inc = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int a = __shfl_up_sync(0xffffffffu, inc.x, o);
         const int b = __shfl_up_sync(0xffffffffu, inc.y, o);
+        const int c = __shfl_up_sync(0xffffffffu, inc.z, o);
         if (lane >= o) {
             inc.x += a;
             inc.y += b;
+            inc.z += c;
         }
     }
     if (lane == 31) warp_s[warp] = inc;
     __syncthreads();
     if (warp == 0) {
         constexpr int NW = T / 32;
-        const int2 w = lane < NW ? warp_s[lane] : make_int2(0, 0);
-        int2 winc = w;
+        const int4 w = lane < NW ? warp_s[lane] : make_int4(0, 0, 0, 0);
+        int4 winc = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int a = __shfl_up_sync(0xffffffffu, winc.x, o);
             const int b = __shfl_up_sync(0xffffffffu, winc.y, o);
+            const int c = __shfl_up_sync(0xffffffffu, winc.z, o);
             if (lane >= o) {
                 winc.x += a;
                 winc.y += b;
+                winc.z += c;
             }
         }
-        if (lane < NW) warp_s[lane] = make_int2(winc.x - w.x, winc.y - w.y);
+        if (lane < NW) warp_s[lane] = make_int4(winc.x - w.x, winc.y - w.y, winc.z - w.z, 0);
         if (lane == NW - 1) *total = winc;
     }
     __syncthreads();
-    const int2 base = warp_s[warp];
-    return make_int2(base.x + inc.x, base.y + inc.y);
+    const int4 base = warp_s[warp];
+    return make_int4(base.x + inc.x, base.y + inc.y, base.z + inc.z, 0);
 }
 
 // First index h in [0, T) with a[h] > x, for an ascending array whose last
@@ -305,18 +322,20 @@ __device__ __forceinline__ void load_one(const AssignParams &P, int pos, int &id
     }
 }
 
-// Register budget: resident CTAs per SM at 128 threads (scaled for other
-// block sizes). 12 caps a thread at 40 registers; on the 300K x 100K,
-// k = 1000 corpus it beat 10 (48 registers) and 8 (64) by 1-3 % (FP32) and
-// 3-9 % (BF16) per assignment, the extra resident warps outweighing the few
-// spilled values.
-#ifndef SIVF_ASSIGN_MIN_CTAS_128
-#define SIVF_ASSIGN_MIN_CTAS_128 12
+// Register budget: 32 resident warps per SM asked of the compiler, so a
+// thread has 64 registers whatever the block size. The dense-row phase keeps
+// 16 FP32 accumulators per thread; with 40 registers (the earlier budget of
+// 48 warps) its loop spilled. 512-thread CTAs serve large k, whose score
+// vector (80 KB at k = 20,000) admits two CTAs per SM anyway: on the
+// 8M x 140K, k = 20,000 corpus (BF16, sparse scan only) asking for three (42
+// registers) took 4.2-4.6 s per assignment, two 3.1-3.3 s, one (128
+// registers, half the warps) 5.5-5.9 s.
+#ifndef SIVF_ASSIGN_WARPS_PER_SM
+#define SIVF_ASSIGN_WARPS_PER_SM 32
 #endif
-// resident CTAs asked of the compiler for a block size (an SM holds at most 32)
 template <int T>
 constexpr int assign_min_blocks() {
-    constexpr int b = SIVF_ASSIGN_MIN_CTAS_128 * 128 / T;
+    constexpr int b = SIVF_ASSIGN_WARPS_PER_SM * 32 / T;
     return b < 1 ? 1 : (b > 32 ? 32 : b);
 }
 
@@ -334,13 +353,90 @@ __device__ __forceinline__ void rho_zero(uint32_t *p) {
     else *p = 0u;
 }
 
+// Dense head rows: 8 consecutive entries (one 16-byte load for BF16/FP16, two
+// for FP32) decoded to FP32. FP16 rows hold u * 2^14 (the scale is folded into
+// the object value by the caller).
+template <int PREC>
+__device__ __forceinline__ void load_dense8(const void *dense, int64_t e, float u[8]) {
+    if constexpr (PREC == SIVF_FP32) {
+        const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float *>(dense) + e);
+        const float4 a = __ldg(p), b = __ldg(p + 1);
+        u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
+        u[4] = b.x; u[5] = b.y; u[6] = b.z; u[7] = b.w;
+    } else {
+        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(static_cast<const uint16_t *>(dense) + e));
+        const unsigned ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            if constexpr (PREC == SIVF_BF16) {
+                u[2 * m] = __uint_as_float(ws[m] << 16);
+                u[2 * m + 1] = __uint_as_float(ws[m] & 0xFFFF0000u);
+            } else {
+                const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&ws[m]));
+                u[2 * m] = f.x;
+                u[2 * m + 1] = f.y;
+            }
+        }
+    }
+}
+
+// Dense phase of one staged chunk: every thread owns 8-entry groups of scan
+// positions (group c * T + tid of each pass) and accumulates, in FP32
+// registers, v * u over the chunk's dense terms in staging order; each
+// position's partial sum is then added to the score as one fixed-point value.
+// Positions [0, npos) are covered: the moving clusters for a front scan, all
+// of the instance's clusters otherwise. A position's sum depends only on the
+// chunk's terms, never on which thread or pass covers it, so front and full
+// scans give the same scores.
+constexpr int DENSE_NCH = 2;  // 8-entry groups per thread and pass
+template <int T, int PREC, bool GRHO>
+__device__ __forceinline__ void dense_chunk(const AssignParams &P, uint32_t *rho, const int2 *s_dense, int nd,
+                                            int npos) {
+    constexpr int PER_PASS = 8 * DENSE_NCH * T;
+    for (int base = 0; base < npos; base += PER_PASS) {
+        float acc[DENSE_NCH][8];
+#pragma unroll
+        for (int c = 0; c < DENSE_NCH; ++c)
+#pragma unroll
+            for (int m = 0; m < 8; ++m) acc[c][m] = 0.f;
+        for (int d = 0; d < nd; ++d) {
+            const int2 e = s_dense[d];
+            const float vs = __int_as_float(e.y);
+            const int64_t row = (int64_t)e.x * 8;
+#pragma unroll
+            for (int c = 0; c < DENSE_NCH; ++c) {
+                const int p = base + (c * T + (int)threadIdx.x) * 8;
+                if (p < npos) {  // rows are padded to multiples of 8: the load stays in the row
+                    float u[8];
+                    load_dense8<PREC>(P.dense, row + p, u);
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) acc[c][m] = fmaf(vs, u[m], acc[c][m]);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < DENSE_NCH; ++c) {
+            const int p = base + (c * T + (int)threadIdx.x) * 8;
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+                if (p + m < npos && acc[c][m] > 0.f) atomicAdd(rho + p + m, __float2uint_ru(acc[c][m]));
+        }
+    }
+}
+
 // GRHO: the score vector lives in global memory (a kmax slab per CTA, L2
 // atomics) instead of shared memory; slower per posting, but independent of
 // the shared-memory size, so it serves any k and lets more CTAs reside.
 // CB: IVF-CBICP (Algorithm 3) instead of SIVF (Algorithm 4). A filtered
 // object then traverses every posting of an unstructured file (ascending
 // centroid ids) and a per-posting branch on lambda^[r-1] skips the invariant
-// centroids; the scores and labels are the same.
+// centroids; the scores and labels are the same. Its score vector keeps
+// cluster-id order and it uses no dense rows.
+//
+// Scores are indexed by scan position (clu_pos / pos_clu): within the
+// instance, the moving clusters of lambda^[r-1] occupy positions
+// 0 .. n_mov - 1 in ascending id, the invariant ones the rest. The candidates
+// of a filtered object are therefore the positions below n_mov.
 template <int T, int PREC, bool CID16, bool GRHO, bool CB = false>
 __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_kernel(AssignParams P) {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -349,14 +445,15 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
     uint32_t *rho = GRHO ? P.grho + (size_t)blockIdx.x * kpad : smem;
     // staged segment of thread h: {scan start, full-block end, end of the full
     // fully scanned blocks, scaled value bits}, scanned length, item and
-    // row-posting prefixes
+    // row-posting prefixes; dense terms of the chunk: {row / 8, scaled value}
     int4 *s_seg = reinterpret_cast<int4 *>(GRHO ? smem : smem + kpad);
-    int *s_len = reinterpret_cast<int *>(s_seg + T);
+    int2 *s_dense = reinterpret_cast<int2 *>(s_seg + T);
+    int *s_len = reinterpret_cast<int *>(s_dense + T);
     int *s_item = s_len + T;
     int *s_rend = s_item + T;
     uint32_t *s_lam = reinterpret_cast<uint32_t *>(s_rend + T);  // CB: lambda^[r-1] bits of all clusters
-    __shared__ int2 warp_i2[32];
-    __shared__ int2 s_total2;
+    __shared__ int4 warp_i4[32];
+    __shared__ int4 s_total4;
     __shared__ long long s_obj;
     __shared__ Top2 warp_t[NW];
     __shared__ double warp_d[NW];
@@ -375,10 +472,11 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
         }
     }
     // per-CTA counters in shared memory (written by one thread or by lane 0
-    // of each warp): filtered, sim-calcs, changed, re-scored, re-score candidates
-    __shared__ unsigned long long s_cnt[5];
-    if (tid < 5) s_cnt[tid] = 0ull;
-    unsigned long long c_post_obj = 0;
+    // of each warp): filtered, sim-calcs, changed, re-scored, re-score
+    // candidates, dense-row entries read
+    __shared__ unsigned long long s_cnt[6];
+    if (tid < 6) s_cnt[tid] = 0ull;
+    unsigned long long c_post_obj = 0, c_dpost = 0;
     __syncthreads();
 
     for (;;) {
@@ -386,7 +484,12 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
         __syncthreads();
         const int64_t i = s_obj;
         if (i >= P.N) break;
-        const int64_t rb = P.row_ptr[i], re = P.row_ptr[i + 1];
+        int64_t rb = P.row_ptr[i], re = P.row_ptr[i + 1];
+        if (P.checked && (rb < 0 || re < rb || re > P.nnz)) {
+            // the borrowed CSR changed since it was validated: record it, read nothing
+            if (tid == 0) atomicOr(&P.ctr->error, 1ull);
+            rb = re = 0;
+        }
         // instance of object i: largest m with inst_obj[m] <= i
         int inst = 0;
         {
@@ -401,11 +504,15 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
         const int km = P.inst_k[inst + 1] - k_off;
         const int32_t a_prev = P.labels_prev[i];  // global id, -1 before the first assignment
         const int a_loc = a_prev >= 0 ? a_prev - k_off : -1;
+        const int a_pos = a_prev < 0 ? -1 : (CB ? a_loc : P.clu_pos[a_prev]);  // index of its score
         const uint32_t own_q = P.own[i];
         const bool filt = P.icp && a_prev >= 0 && own_q != OWN_INVALID && P.lam_prev[a_prev] != 0;
         const int mb = P.mov_beg[inst];
         const int n_mov_inst = P.mov_beg[inst + 1] - mb;
         const int32_t *movs = P.mov_list + mb;
+        // score index of the m-th moving cluster, and cluster id of a score index
+        auto mov_at = [&](int m) { return CB ? movs[m] - k_off : m; };
+        auto id_at = [&](int p) { return CB ? p : P.pos_clu[k_off + p]; };
         // relaxed filter (icp = 3): the own cluster moved, and at most half of
         // the instance's clusters are moving; decided after the front scan
         bool relax = P.icp == 3 && !filt && a_prev >= 0 && own_q != OWN_INVALID && 2 * n_mov_inst <= km;
@@ -428,19 +535,21 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
             if (!cbf || !((s_lam[(k_off + id) >> 5] >> ((k_off + id) & 31)) & 1u))
                 atomicAdd(&rho[id], __float2uint_ru(prod));
         };
+        int nd_obj = 0;  // dense terms of the object (error bound)
 
         // ---- similarity scan (Algorithm 4, lines 7-13) ----
-        // The object's terms are staged T at a time. Each segment (the part of
-        // a term's posting list that is scanned: the front, or the whole list)
-        // splits into its full 128-entry blocks of the tiled layout whose
-        // postings are all scanned, and a remainder of fewer than 128
-        // postings (the part of a block that a front ends inside, or the
-        // list's ragged tail). Work is done in two forms:
+        // The object's terms are staged T at a time. A term with a dense row
+        // is accumulated from it (dense_chunk). Every other term's segment
+        // (the part of its posting list that is scanned: the front, or the
+        // whole list) splits into its full 128-entry blocks of the tiled
+        // layout whose postings are all scanned, and a remainder of fewer
+        // than 128 postings (the part of a block that a front ends inside, or
+        // the list's ragged tail). Work is done in two forms:
         //  - items: two full blocks (the last one of a segment may hold one),
         //    or a remainder of at least RMIN postings. In a full block lane l
         //    reads postings l, 32+l, 64+l, 96+l with one vector load per
         //    array; step m of the warp then touches postings 32m .. 32m+31,
-        //    whose ids are distinct banks on dense lists. Warp w takes a
+        //    whose positions are distinct banks on dense lists. Warp w takes a
         //    contiguous range of the items;
         //  - rows: the shorter remainders of all staged segments are laid end
         //    to end and cut into rows of 32 postings, one posting per lane, so
@@ -449,28 +558,53 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
         constexpr int RMIN = 16;
         for (int pass = 0;; ++pass) {
         const bool front = (filt || relax) && pass == 0;  // scan the fronts only
+        const int npos = front ? n_mov_inst : km;         // score positions this pass covers
         for (int64_t cb = rb; cb < re; cb += T) {
             const int cn = (int)min((int64_t)T, re - cb);
-            int2 cnt = make_int2(0, 0);
+            int4 cnt = make_int4(0, 0, 0, 0);
+            int2 dent = make_int2(-1, 0);
             if (tid < cn) {
-                const int t = P.idx[cb + tid];
-                const int64_t o0 = P.if_off[t];
-                const int lfull = (int)(P.if_off[t + 1] - o0);
-                const int len = (front && !CB) ? P.if_mf0[t] : lfull;
-                const int fb = lfull & ~(SC_BLK - 1);
-                const int r0 = min(len, fb) & ~(SC_BLK - 1);  // postings in full, fully scanned blocks
-                const float vs = P.val[cb + tid] * FIX_SCALE;  // exact: power-of-two scaling
-                s_seg[tid] = make_int4((int)P.sc_off[t], fb, r0, __float_as_int(vs));
-                s_len[tid] = len;
-                const int rem = len - r0;
-                cnt = rem >= RMIN ? make_int2((r0 + CH - 1) / CH + 1, 0) : make_int2((r0 + CH - 1) / CH, rem);
+                int t = P.idx[cb + tid];
+                if (P.checked && (t < 0 || t >= P.D)) {  // a term outside [0, D): record it, skip it
+                    atomicOr(&P.ctr->error, 2ull);
+                    t = -1;
+                }
+                const int64_t o0 = t >= 0 ? P.if_off[t] : 0;
+                const int lfull = t >= 0 ? (int)(P.if_off[t + 1] - o0) : 0;
+                const int len = t < 0 ? 0 : ((front && !CB) ? P.if_mf0[t] : lfull);
+                float vs = P.val[cb + tid] * FIX_SCALE;  // exact: power-of-two scaling
+                const int dr = (CB || t < 0) ? -1 : P.dense_row[t];
                 c_post_obj += (unsigned long long)len;
+                if (dr >= 0) {  // dense row: no segment to scan
+                    if constexpr (PREC == SIVF_FP16) vs *= FP16_INV_SCALE;  // rows hold u * 2^14 (exact)
+                    dent = make_int2(dr, __float_as_int(vs));
+                    cnt.z = 1;
+                    c_dpost += (unsigned long long)len;
+                    s_seg[tid] = make_int4(0, 0, 0, 0);
+                    s_len[tid] = 0;
+                } else {
+                    const int fb = lfull & ~(SC_BLK - 1);
+                    const int r0 = min(len, fb) & ~(SC_BLK - 1);  // postings in full, fully scanned blocks
+                    s_seg[tid] = make_int4(t >= 0 ? (int)P.sc_off[t] : 0, fb, r0, __float_as_int(vs));
+                    s_len[tid] = len;
+                    const int rem = len - r0;
+                    cnt.x = rem >= RMIN ? (r0 + CH - 1) / CH + 1 : (r0 + CH - 1) / CH;
+                    cnt.y = rem >= RMIN ? 0 : rem;
+                }
             }
-            const int2 incl = block_inclusive_scan_int2<T>(cnt, warp_i2, &s_total2);
+            const int4 incl = block_inclusive_scan_int4<T>(cnt, warp_i4, &s_total4);
             s_item[tid] = incl.x;
             s_rend[tid] = incl.y;
+            if (dent.x >= 0) s_dense[incl.z - 1] = dent;  // dense terms in staging order
             __syncthreads();
-            const int2 tot = s_total2;
+            const int4 tot = s_total4;
+
+            // dense rows
+            if (tot.z > 0) {
+                nd_obj += tot.z;
+                dense_chunk<T, PREC, GRHO>(P, rho, s_dense, tot.z, npos);
+                if (tid == 0) s_cnt[5] += (unsigned long long)tot.z * (unsigned long long)npos;
+            }
 
             // items
             {
@@ -575,33 +709,42 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
         // rho~_new - E(rho~_new) >= rho~_old + E(rho~_old), which implies it
         // for the exact scores; otherwise scan everything again.
         if (tid == 0) {
-            const double xn = (double)rho_ld<GRHO>(rho + a_loc) * FIX_QUANTUM;
+            const double xn = (double)rho_ld<GRHO>(rho + a_pos) * FIX_QUANTUM;
             const double xo = (double)own_q * FIX_QUANTUM;
             const double S = (double)P.sumv[i];
-            s_flag = xn - error_bound(xn, re - rb, S, P.eps, P.eta) >= xo + error_bound(xo, re - rb, S, P.eps, P.eta);
+            // the old score came from an earlier scan, whose dense terms may
+            // have differed: bound it with every term counted as dense
+            s_flag = xn - error_bound(xn, re - rb, nd_obj, S, P.eps, P.eta) >=
+                     xo + error_bound(xo, re - rb, (int)(re - rb), S, P.eps, P.eta);
         }
         __syncthreads();
         if (s_flag) break;
-        for (int m = tid; m < n_mov_inst; m += T) rho_zero<GRHO>(rho + (movs[m] - k_off));
+        for (int m = tid; m < n_mov_inst; m += T) rho_zero<GRHO>(rho + mov_at(m));
         __syncthreads();
         relax = false;
         wasted = true;
+        nd_obj = 0;  // the full scan counts its dense terms again
         }
         const bool sub = filt || relax;  // candidates: the moving clusters (plus the carried own one if filt)
         const int n_mov = sub ? n_mov_inst : 0;
 
         // ---- argmax over the candidates (Algorithm 4, lines 14-16) ----
+        // largest score, lowest cluster id on ties (ids are looked up only
+        // when a score ties or beats the running best)
         Top2 t;
         t.bv = 0u;
         t.bi = INT32_MAX;
         t.sv = -1;
-        // candidates by local id (same order as global ids within the instance)
+        auto push = [&](uint32_t v, int p) {
+            if (t.bi == INT32_MAX || v >= t.bv) top2_push(t, v, id_at(p));
+            else t.sv = max(t.sv, (long long)v);
+        };
         if (!sub) {
-            for (int j = tid; j < km; j += T) top2_push(t, rho_ld<GRHO>(rho + j), j);
+            for (int p = tid; p < km; p += T) push(rho_ld<GRHO>(rho + p), p);
         } else {
             for (int m = tid; m < n_mov; m += T) {
-                const int j = movs[m] - k_off;
-                top2_push(t, rho_ld<GRHO>(rho + j), j);
+                const int p = mov_at(m);
+                push(rho_ld<GRHO>(rho + p), p);
             }
             if (tid == 0) top2_push(t, own_q, a_loc);
         }
@@ -616,7 +759,10 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
             uint32_t thr = 0;
             if (b.bv > 0u && b.sv >= 0) {
                 const double best = (double)b.bv * FIX_QUANTUM;
-                const double E = error_bound(best, re - rb, (double)P.sumv[i], P.eps, P.eta);
+                // a filtered object's carried own score may come from a scan with
+                // other dense terms: count every term as dense for it
+                const double E = error_bound(best, re - rb, filt ? (int)(re - rb) : nd_obj, (double)P.sumv[i],
+                                             P.eps, P.eta);
                 const double gap = (double)((long long)b.bv - b.sv) * FIX_QUANTUM;
                 if (gap <= 2.0 * E) {
                     flag = 1;
@@ -641,8 +787,8 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
                 const int m = base + lane;
                 int j = -1;
                 if (m < total) {
-                    j = sub ? movs[m] - k_off : m;
-                    if (rho_ld<GRHO>(rho + j) < thr) j = -1;
+                    const int p = sub ? mov_at(m) : m;
+                    if (rho_ld<GRHO>(rho + p) >= thr) j = id_at(p);
                 }
                 unsigned bal = __ballot_sync(0xffffffffu, j >= 0);
                 while (bal) {
@@ -691,7 +837,7 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
             const int al = s_winner;  // local id
             const int a = k_off + al;
             P.labels[i] = a;
-            P.own[i] = (filt && al == a_loc) ? own_q : rho_ld<GRHO>(rho + al);
+            P.own[i] = (filt && al == a_loc) ? own_q : rho_ld<GRHO>(rho + (CB ? al : P.clu_pos[a]));
             if (a != a_prev) {
                 s_cnt[2] += 1;
                 P.moving[a] = 1;
@@ -704,17 +850,21 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
         }
         __syncthreads();
         if (!sub) {
-            for (int j = tid; j < km; j += T) rho_zero<GRHO>(rho + j);
+            for (int p = tid; p < km; p += T) rho_zero<GRHO>(rho + p);
         } else {
-            for (int m = tid; m < n_mov; m += T) rho_zero<GRHO>(rho + (movs[m] - k_off));
+            for (int m = tid; m < n_mov; m += T) rho_zero<GRHO>(rho + mov_at(m));
         }
         __syncthreads();
     }
 
     // every thread staged a share of the terms: sum the posting counts
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c_post_obj += __shfl_xor_sync(0xffffffffu, c_post_obj, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        c_post_obj += __shfl_xor_sync(0xffffffffu, c_post_obj, o);
+        c_dpost += __shfl_xor_sync(0xffffffffu, c_dpost, o);
+    }
     if (lane == 0 && c_post_obj) atomicAdd(&P.ctr->postings, c_post_obj);
+    if (lane == 0 && c_dpost) atomicAdd(&P.ctr->dense_postings, c_dpost);
     __syncthreads();
     if (tid == 0) {
         atomicAdd(&P.ctr->filtered, s_cnt[0]);
@@ -724,6 +874,7 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
             atomicAdd(&P.ctr->rescored, s_cnt[3]);
             atomicAdd(&P.ctr->rescore_cands, s_cnt[4]);
         }
+        if (s_cnt[5]) atomicAdd(&P.ctr->dense_entries, s_cnt[5]);
     }
 }
 
@@ -817,6 +968,9 @@ cudaError_t launch_assign(sivf_ctx *c) {
     P.N = c->N;
     P.k = c->k;
     P.icp = c->cfg.icp;
+    P.checked = c->cfg.checked ? 1 : 0;
+    P.D = c->D;
+    P.nnz = c->nnz;
     P.row_ptr = c->row_ptr;
     P.idx = c->idx;
     P.val = c->val;
@@ -829,6 +983,10 @@ cudaError_t launch_assign(sivf_ctx *c) {
     P.sc_val = c->sc_val;
     P.sc_pack = c->sc_pack;
     P.sc_lp = c->sc_lp;
+    P.clu_pos = c->clu_pos;
+    P.pos_clu = c->pos_clu;
+    P.dense_row = c->dense_row;
+    P.dense = c->dense_val;
     P.grho = c->grho;
     P.coff = c->coff[c->cur];
     P.cterm = c->cterm[c->cur];

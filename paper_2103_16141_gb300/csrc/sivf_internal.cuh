@@ -20,10 +20,26 @@
 //                                        block position 4l + m), so that lane l reads
 //                                        entries l, 32+l, 64+l, 96+l with one vector
 //                                        load; the ragged tail keeps canonical order.
-//                                        Arrays (local cluster ids): sc_id16 u16 or
+//                                        Arrays (scan positions): sc_id16 u16 or
 //                                        sc_id32 int32, plus sc_val f32 (FP32), or
 //                                        sc_pack u32 = id << 16 | bf16/fp16 value
 //                                        (16-bit ids and values), or sc_lp u16
+//                                        Ids in the scan copy are scan positions (below).
+//   scan order            clu_pos int32[k]: position of cluster j in its instance's
+//                                        scan order (moving clusters of lambda^[r] first,
+//                                        ascending id, then the invariant ones, ascending
+//                                        id); pos_clu int32[k]: the inverse (instance
+//                                        offset + position -> local id). Score vectors are
+//                                        indexed by position. IVF-CBICP keeps id order.
+//   dense head rows       dense_row int32[D]: first entry / 8 of term t's dense row, or
+//                                        -1 (the term is scanned from the sparse copy);
+//                                        dense_val (u16 or f32) [cap_dense]: one row per dense
+//                                        term, the term's value for every cluster of its
+//                                        instance at the cluster's scan position (0 where
+//                                        the cluster lacks the term), padded to a multiple
+//                                        of 8 entries; a term's list becomes a row when it
+//                                        holds at least dense_frac of its instance's k
+//                                        (raised while the rows would exceed cap_dense).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -43,8 +59,8 @@ constexpr int64_t IF_PAD = 256;
 constexpr int SC_BLK = 128;
 // shared memory the assignment kernel stages per thread besides the score
 // vector: list start, full-block end, end of the full scanned blocks, scaled
-// value, scanned length, item prefix, row-posting prefix
-constexpr int ASSIGN_STAGE_BYTES = 28;
+// value, scanned length, item prefix, row-posting prefix, dense row and value
+constexpr int ASSIGN_STAGE_BYTES = 36;
 // Scores are accumulated as unsigned fixed point with quantum 2^-31:
 // q = ceil(fl(v * u) * 2^31). Cosine scores are <= 1 (+ rounding), so the
 // sum of an object's terms stays below 2^32.
@@ -67,7 +83,11 @@ struct DevCounters {
     unsigned long long error;        // nonzero: device-side check failed (code)
     long long moved;                 // object non-zeros gathered by the last update
     long long c_nnz;                 // centroid non-zeros after the last update
-    unsigned long long pad[5];
+    unsigned long long dense_entries;   // dense-row entries read by the assignment
+    unsigned long long dense_postings;  // postings of the scanned segments held in dense rows
+    long long dense_terms;              // terms with a dense row (last inverted-file build)
+    long long dense_used;               // dense-row entries in use / 8 (last build)
+    unsigned long long pad[1];
 };
 
 // Bump allocator over one device block (scratch that lives for one step).
@@ -139,6 +159,15 @@ struct sivf_ctx {
     uint32_t *sc_pack = nullptr;  // 16-bit ids and 16-bit values
     uint16_t *sc_lp = nullptr;    // 32-bit ids and 16-bit values
     int64_t cap_s = 0;            // entries of each scan array
+    // scan order and dense head rows (see the layout above)
+    int32_t *clu_pos = nullptr, *pos_clu = nullptr;
+    int32_t *dense_row = nullptr;
+    void *dense_val = nullptr;    // dense rows: u16 (BF16/FP16) or f32 entries
+    int64_t cap_dense = 0;        // entries of dense (0: no dense rows)
+    float dense_frac = 0.f;       // list length / k from which a term gets a dense row
+    int32_t *inst_d = nullptr;    // device [n_inst+1]: first term of each instance
+    int32_t *dense_thr = nullptr; // device [1]: threshold bin chosen by the last build
+    long long dense_terms_h = 0, dense_used_h = 0;
 
     // dense update accumulator: cluster j owns acc[acc_off[j] .. acc_off[j+1]),
     // one int64 per term of its instance, in units of 2^-acc_shift. It holds

@@ -690,9 +690,10 @@ __global__ void k_if_fill(const int64_t *n_dev, int64_t cap, const uint32_t *ord
 }
 
 // Scan copy of the file, one warp per segment (the front or the back of a
-// list). Inside a segment the postings are reordered so that 32 consecutive
-// ones fall on distinct shared-memory banks of the score vector (bank =
-// local id mod 32) as far as the segment allows: by rank among the segment's
+// list) of every term without a dense row. The copy holds each posting's scan
+// position (the index of its score). Inside a segment the postings are
+// reordered so that 32 consecutive ones fall on distinct shared-memory banks
+// of the score vector (bank = position mod 32) as far as the segment allows: by rank among the segment's
 // postings of the same bank, then by bank. Consecutive ranks then cover every
 // bank once while all banks last, and a window of 32 that straddles two such
 // ranks still does. The order inside a part does not change any score (each
@@ -701,8 +702,8 @@ __global__ void k_if_fill(const int64_t *n_dev, int64_t cap, const uint32_t *ord
 constexpr int SC_COPY_THREADS = 256;
 __global__ void __launch_bounds__(SC_COPY_THREADS) k_if_scan_copy(
     int32_t D, const int64_t *if_off, const int32_t *if_mf0, const int64_t *sc_off, const int32_t *if_cid,
-    const float *if_val, const int32_t *clu_koff, int prec, uint16_t *sc_id16, int32_t *sc_id32, float *sc_val,
-    uint32_t *sc_pack, uint16_t *sc_lp) {
+    const float *if_val, const int32_t *clu_pos, const int32_t *dense_row, int prec, uint16_t *sc_id16,
+    int32_t *sc_id32, float *sc_val, uint32_t *sc_pack, uint16_t *sc_lp) {
     __shared__ int s_cnt[SC_COPY_THREADS / 32][32];
     __shared__ int s_run[SC_COPY_THREADS / 32][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -710,6 +711,7 @@ __global__ void __launch_bounds__(SC_COPY_THREADS) k_if_scan_copy(
     const int64_t nw = ((int64_t)gridDim.x * SC_COPY_THREADS) >> 5;
     for (int64_t seg = (blockIdx.x * (int64_t)SC_COPY_THREADS + threadIdx.x) >> 5; seg < 2 * (int64_t)D; seg += nw) {
         const int t = (int)(seg >> 1);
+        if (dense_row[t] >= 0) continue;  // read from its dense row instead
         const int64_t o = if_off[t];
         const int L = (int)(if_off[t + 1] - o), m0 = if_mf0[t];
         const int s0 = (seg & 1) ? m0 : 0, n = (seg & 1) ? L - m0 : m0;
@@ -720,7 +722,7 @@ __global__ void __launch_bounds__(SC_COPY_THREADS) k_if_scan_copy(
         for (int c0 = 0; c0 < n; c0 += 32) {  // postings per bank
             if (c0 + lane < n) {
                 const int32_t j = if_cid[o + s0 + c0 + lane];
-                atomicAdd(&s_cnt[w][(j - clu_koff[j]) & 31], 1);
+                atomicAdd(&s_cnt[w][clu_pos[j] & 31], 1);
             }
         }
         __syncwarp();
@@ -730,7 +732,7 @@ __global__ void __launch_bounds__(SC_COPY_THREADS) k_if_scan_copy(
             const bool ok = c0 + lane < n;
             const int64_t q = o + s0 + c0 + lane;
             const int32_t j = ok ? if_cid[q] : 0;
-            const uint32_t jl = ok ? (uint32_t)(j - clu_koff[j]) : 0u;
+            const uint32_t jl = ok ? (uint32_t)clu_pos[j] : 0u;  // the posting's scan position
             const int bank = (int)(jl & 31);
             const unsigned peers = __match_any_sync(0xffffffffu, ok ? bank : 32 + lane);
             const int rank = (ok ? s_run[w][bank] : 0) + __popc(peers & below);
@@ -762,6 +764,143 @@ __global__ void __launch_bounds__(SC_COPY_THREADS) k_if_scan_copy(
             }
             if (sc_pack) sc_pack[pos] = (jl << 16) | (uint32_t)lp;
             else sc_lp[pos] = lp;
+        }
+    }
+}
+
+// ---------------- scan order and dense head rows ----------------
+
+// Scan position of every cluster: within its instance, the moving clusters of
+// lambda^[r] (mov_list, ascending) take positions 0 .. n_mov - 1 and the
+// invariant ones follow in ascending id; id_order (IVF-CBICP) keeps the ids.
+__global__ void k_positions(int32_t k, int32_t n_inst, const int32_t *inst_k, const uint8_t *lam,
+                            const int32_t *mov_list, const int32_t *mov_beg, int id_order, int32_t *clu_pos,
+                            int32_t *pos_clu) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < k; g += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t j = (int32_t)g;
+        int lo = 0, hi = n_inst - 1;  // instance: largest m with inst_k[m] <= j
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (inst_k[mid] <= j) lo = mid; else hi = mid - 1;
+        }
+        const int32_t koff = inst_k[lo], jl = j - koff;
+        int32_t p = jl;
+        if (!id_order) {
+            const int32_t b = mov_beg[lo], e = mov_beg[lo + 1];
+            int32_t a = b, z = e;  // first moving id >= j
+            while (a < z) {
+                const int32_t mid = (a + z) >> 1;
+                if (mov_list[mid] < j) a = mid + 1; else z = mid;
+            }
+            p = lam[j] == 0 ? a - b : (e - b) + (jl - (a - b));
+        }
+        clu_pos[j] = p;
+        pos_clu[koff + p] = jl;
+    }
+}
+
+constexpr int DENSE_BINS = 64;      // list length / k in steps of 1/64
+constexpr int DENSE_MIN_LEN = 32;   // shorter lists stay sparse whatever k
+
+// instance of term t, its k, and the 1/64 bin of its list length
+__device__ __forceinline__ void term_bin(int32_t t, int32_t n_inst, const int32_t *inst_d, const int32_t *inst_k,
+                                         int64_t L, int32_t *kin, int *bin) {
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (inst_d[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int32_t km = inst_k[lo + 1] - inst_k[lo];
+    *kin = km;
+    const int64_t q = (L * DENSE_BINS) / (km > 0 ? km : 1);
+    *bin = (int)(q < DENSE_BINS ? q : DENSE_BINS);
+}
+
+// Histogram of the dense-row entries each length bin would take.
+__global__ void k_dense_hist(int32_t D, int32_t n_inst, const int32_t *inst_d, const int32_t *inst_k,
+                             const int64_t *len, unsigned long long *hist) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < D; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t L = len[g];
+        if (L < DENSE_MIN_LEN) continue;
+        int32_t km;
+        int bin;
+        term_bin((int32_t)g, n_inst, inst_d, inst_k, L, &km, &bin);
+        atomicAdd(hist + bin, (unsigned long long)((km + 7) & ~7));
+    }
+}
+
+// Smallest bin >= bmin whose rows (with every longer bin's) fit in cap
+// entries; DENSE_BINS + 1 = no dense rows.
+__global__ void k_dense_threshold(const unsigned long long *hist, int bmin, unsigned long long cap, int32_t *thr) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long acc = 0;
+    int b = DENSE_BINS + 1;
+    for (int q = DENSE_BINS; q >= bmin; --q) {
+        acc += hist[q];
+        if (acc > cap) break;
+        b = q;
+    }
+    *thr = b;
+}
+
+// Dense-row width (in 8-entry units) of every term; the sparse scan copy
+// gives dense terms no room.
+__global__ void k_dense_width(int32_t D, int32_t n_inst, const int32_t *inst_d, const int32_t *inst_k,
+                              const int64_t *len, const int32_t *thr, int64_t *w8, int64_t *slen) {
+    const int b = *thr;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < D; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t L = len[g];
+        int64_t w = 0;
+        if (L >= DENSE_MIN_LEN) {
+            int32_t km;
+            int bin;
+            term_bin((int32_t)g, n_inst, inst_d, inst_k, L, &km, &bin);
+            if (bin >= b) w = (km + 7) >> 3;
+        }
+        w8[g] = w;
+        if (w) slen[g] = 0;
+    }
+}
+
+__global__ void k_dense_rows(int32_t D, const int64_t *w8, const int64_t *base8, int32_t *dense_row,
+                             DevCounters *ctr) {
+    long long n = 0;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < D; g += (int64_t)gridDim.x * blockDim.x) {
+        const bool d = w8[g] > 0;
+        dense_row[g] = d ? (int32_t)base8[g] : -1;
+        n += d;
+    }
+    if (n) atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->dense_terms), (unsigned long long)n);
+}
+
+// zero the entries in use (16 bytes at a time; rows are multiples of 8 entries)
+__global__ void k_dense_zero(const int64_t *used8, int esize, uint4 *dense) {
+    const int64_t n16 = used8[0] * 8 * esize / 16;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n16; q += (int64_t)gridDim.x * blockDim.x)
+        dense[q] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// One warp per dense term: every posting's value at its cluster's position.
+__global__ void k_dense_fill(int32_t D, const int32_t *dense_row, const int64_t *if_off, const int32_t *if_cid,
+                             const float *if_val, const int32_t *clu_pos, int prec, void *dense) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < D; t += nw) {
+        const int32_t r = dense_row[t];
+        if (r < 0) continue;
+        const int64_t base = (int64_t)r * 8;
+        for (int64_t q = if_off[t] + lane; q < if_off[t + 1]; q += 32) {
+            const int64_t e = base + clu_pos[if_cid[q]];
+            const float u = if_val[q];
+            if (prec == SIVF_FP32) {
+                static_cast<float *>(dense)[e] = u;
+            } else if (prec == SIVF_BF16) {
+                static_cast<uint16_t *>(dense)[e] = __bfloat16_as_ushort(__float2bfloat16_rn(u));
+            } else {
+                unsigned short h = __half_as_ushort(__float2half_rn(u * FP16_SCALE));
+                if (h == 0 && u > 0.0f) h = 1;  // keep every stored value strictly positive
+                static_cast<uint16_t *>(dense)[e] = h;
+            }
         }
     }
 }
@@ -858,33 +997,71 @@ cudaError_t build_inverted_file(sivf_ctx *c) {
     const int64_t cap = c->cap_c;
     const int cur = c->cur;
     const int64_t *n_dev = c->coff[cur] + c->k;
+    const int32_t D = c->D;
     Workspace &ws = c->ws;
     size_t mark = ws.used;
-    uint32_t *cnt2 = ws.take<uint32_t>((size_t)2 * c->D);
-    int64_t *len = ws.take<int64_t>((size_t)c->D + 1);
-    int64_t *slen = ws.take<int64_t>((size_t)c->D + 1);
-    int64_t *total = ws.take<int64_t>(2);
+    uint32_t *cnt2 = ws.take<uint32_t>((size_t)2 * D);
+    int64_t *len = ws.take<int64_t>((size_t)D + 1);
+    int64_t *slen = ws.take<int64_t>((size_t)D + 1);
+    int64_t *w8 = ws.take<int64_t>((size_t)D + 1);
+    int64_t *base8 = ws.take<int64_t>((size_t)D + 1);
+    unsigned long long *hist = ws.take<unsigned long long>(DENSE_BINS + 1);
+    int64_t *total = ws.take<int64_t>(3);
     uint32_t *k0 = ws.take<uint32_t>((size_t)cap + 1), *v0 = ws.take<uint32_t>((size_t)cap + 1);
     uint32_t *k1 = ws.take<uint32_t>((size_t)cap + 1), *v1 = ws.take<uint32_t>((size_t)cap + 1);
-    if (!cnt2 || !len || !slen || !total || !k0 || !v0 || !k1 || !v1) return cudaErrorMemoryAllocation;
-    SIVF_CUDA_TRY(cudaMemsetAsync(cnt2, 0, sizeof(uint32_t) * 2 * c->D, c->stream));
-    k_if_keys<<<blocks_gs(cap), TPB, 0, c->stream>>>(n_dev, cap, c->cterm[cur], c->cclu, c->lam,
-                                                      c->cfg.icp == 2 ? 0 : 1, k0, v0, cnt2);
-    k_if_lens<<<blocks_for(c->D), TPB, 0, c->stream>>>(c->D, cnt2, len, slen, c->if_mf0);
-    note_launch(2);
+    if (!cnt2 || !len || !slen || !w8 || !base8 || !hist || !total || !k0 || !v0 || !k1 || !v1)
+        return cudaErrorMemoryAllocation;
+    cudaStream_t s = c->stream;
+    const bool cb = c->cfg.icp == 2;
+    SIVF_CUDA_TRY(cudaMemsetAsync(cnt2, 0, sizeof(uint32_t) * 2 * D, s));
+    k_if_keys<<<blocks_gs(cap), TPB, 0, s>>>(n_dev, cap, c->cterm[cur], c->cclu, c->lam, cb ? 0 : 1, k0, v0, cnt2);
+    k_if_lens<<<blocks_for(D), TPB, 0, s>>>(D, cnt2, len, slen, c->if_mf0);
+    // scan order of lambda^[r] (mov_list and mov_beg were computed from it)
+    k_positions<<<blocks_gs(c->k), TPB, 0, s>>>(c->k, c->n_inst, c->inst_k, c->lam, c->mov_list, c->mov_beg,
+                                                 cb ? 1 : 0, c->clu_pos, c->pos_clu);
+    note_launch(3);
+    // dense head rows: the longest lists (relative to their instance's k) that
+    // fit in the row capacity, from dense_frac of k up
+    SIVF_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (DENSE_BINS + 1), s));
+    const int bmin = (int)ceilf(c->dense_frac * DENSE_BINS);
+    const bool dense = c->cap_dense > 0 && !cb && bmin <= DENSE_BINS;
+    if (dense) {
+        k_dense_hist<<<blocks_gs(D), TPB, 0, s>>>(D, c->n_inst, c->inst_d, c->inst_k, len, hist);
+        k_dense_threshold<<<1, 32, 0, s>>>(hist, bmin < 1 ? 1 : bmin, (unsigned long long)c->cap_dense,
+                                          c->dense_thr);
+        note_launch(2);
+    } else {  // no bin qualifies: the threshold becomes DENSE_BINS + 1 (no rows)
+        k_dense_threshold<<<1, 32, 0, s>>>(hist, DENSE_BINS + 1, 0ull, c->dense_thr);
+        note_launch();
+    }
+    k_dense_width<<<blocks_gs(D), TPB, 0, s>>>(D, c->n_inst, c->inst_d, c->inst_k, len, c->dense_thr, w8, slen);
+    note_launch();
     SIVF_CUDA_TRY(cudaGetLastError());
-    SIVF_CUDA_TRY(scan_exclusive_i64(len, c->if_off, c->D, total, ws, c->stream));
-    SIVF_CUDA_TRY(cudaMemcpyAsync(c->if_off + c->D, total, sizeof(int64_t), cudaMemcpyDeviceToDevice, c->stream));
-    SIVF_CUDA_TRY(scan_exclusive_i64(slen, c->sc_off, c->D, total + 1, ws, c->stream));
-    SIVF_CUDA_TRY(cudaMemcpyAsync(c->sc_off + c->D, total + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, c->stream));
+    SIVF_CUDA_TRY(scan_exclusive_i64(len, c->if_off, D, total, ws, s));
+    SIVF_CUDA_TRY(cudaMemcpyAsync(c->if_off + D, total, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    SIVF_CUDA_TRY(scan_exclusive_i64(slen, c->sc_off, D, total + 1, ws, s));
+    SIVF_CUDA_TRY(cudaMemcpyAsync(c->sc_off + D, total + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    SIVF_CUDA_TRY(scan_exclusive_i64(w8, base8, D, total + 2, ws, s));
+    SIVF_CUDA_TRY(cudaMemsetAsync(&c->ctr->dense_terms, 0, sizeof(long long), s));
+    k_dense_rows<<<blocks_gs(D), TPB, 0, s>>>(D, w8, base8, c->dense_row, c->ctr);
+    note_launch();
     bool alt = false;
-    SIVF_CUDA_TRY(radix_sort_pairs_dev(k0, v0, k1, v1, cap, n_dev, c->bits_t + 1, &alt, ws, c->stream));
-    k_if_fill<<<blocks_gs(cap), TPB, 0, c->stream>>>(n_dev, cap, alt ? v1 : v0, c->cclu, c->cval[cur], c->if_cid,
-                                                      c->if_val);
-    k_if_scan_copy<<<blocks_gs((int64_t)2 * c->D * 32, SC_COPY_THREADS), SC_COPY_THREADS, 0, c->stream>>>(
-        c->D, c->if_off, c->if_mf0, c->sc_off, c->if_cid, c->if_val, c->clu_koff, (int)c->cfg.prec, c->sc_id16,
-        c->sc_id32, c->sc_val, c->sc_pack, c->sc_lp);
+    SIVF_CUDA_TRY(radix_sort_pairs_dev(k0, v0, k1, v1, cap, n_dev, c->bits_t + 1, &alt, ws, s));
+    k_if_fill<<<blocks_gs(cap), TPB, 0, s>>>(n_dev, cap, alt ? v1 : v0, c->cclu, c->cval[cur], c->if_cid,
+                                              c->if_val);
+    k_if_scan_copy<<<blocks_gs((int64_t)2 * D * 32, SC_COPY_THREADS), SC_COPY_THREADS, 0, s>>>(
+        D, c->if_off, c->if_mf0, c->sc_off, c->if_cid, c->if_val, c->clu_pos, c->dense_row, (int)c->cfg.prec,
+        c->sc_id16, c->sc_id32, c->sc_val, c->sc_pack, c->sc_lp);
     note_launch(2);
+    if (dense) {
+        const int esize = c->cfg.prec == SIVF_FP32 ? 4 : 2;
+        k_dense_zero<<<blocks_gs(c->cap_dense * esize / 16), TPB, 0, s>>>(total + 2, esize,
+                                                                            static_cast<uint4 *>(c->dense_val));
+        k_dense_fill<<<blocks_gs((int64_t)D * 32), TPB, 0, s>>>(D, c->dense_row, c->if_off, c->if_cid, c->if_val,
+                                                                  c->clu_pos, (int)c->cfg.prec, c->dense_val);
+        note_launch(2);
+    }
+    SIVF_CUDA_TRY(cudaMemcpyAsync(&c->ctr->dense_used, total + 2, sizeof(long long), cudaMemcpyDeviceToDevice, s));
     SIVF_CUDA_TRY(cudaGetLastError());
     ws.used = mark;
     return cudaSuccess;

@@ -35,7 +35,8 @@ class sivf_config(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("icp", ctypes.c_int), ("threads", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("mem_cap_bytes", ctypes.c_int64), ("use_graph", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("score_buffer", ctypes.c_int), ("update_mode", ctypes.c_int),
-                ("inputs_on_host", ctypes.c_int)]
+                ("inputs_on_host", ctypes.c_int), ("checked", ctypes.c_int),
+                ("dense_max_bytes", ctypes.c_int64), ("dense_min_fraction", ctypes.c_float)]
 
 
 class sivf_stats(ctypes.Structure):
@@ -46,7 +47,9 @@ class sivf_stats(ctypes.Structure):
                 ("objective_assign", ctypes.c_double), ("objective_update", ctypes.c_double),
                 ("ms_assign", ctypes.c_double), ("ms_update", ctypes.c_double), ("launches", ctypes.c_int64),
                 ("graph_iters", ctypes.c_int64), ("assign_threads", ctypes.c_int32),
-                ("assign_global", ctypes.c_int32), ("update_dense", ctypes.c_int32)]
+                ("assign_global", ctypes.c_int32), ("update_dense", ctypes.c_int32),
+                ("dense_entries", ctypes.c_int64), ("dense_postings", ctypes.c_int64),
+                ("dense_terms", ctypes.c_int64), ("dense_row_entries", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -123,6 +126,9 @@ def load(build_if_missing: bool = True):
         lib.sivf_batch_instance_stats.restype = st
         lib.sivf_build_inverted_file_noalloc.argtypes = [i32, i32, i64, p, p, p, p, p, p, p, p, p]
         lib.sivf_build_inverted_file_noalloc.restype = st
+        lib.sivf_measure_read_bandwidth.argtypes = [p, i64, i32, p, ctypes.POINTER(ctypes.c_double),
+                                                    ctypes.POINTER(ctypes.c_double)]
+        lib.sivf_measure_read_bandwidth.restype = st
         _lib = lib
         return lib
 
@@ -195,6 +201,16 @@ def sivf_build_inverted_file_noalloc(k: int, D: int, n_entries: int, coff: int, 
                                                            if_cid, if_u, stream))
 
 
+def sivf_measure_read_bandwidth(buf: int, nbytes: int, passes: int, stream: int):
+    """(GB/s, ms) of `passes` streaming reads of a 16-byte-aligned device
+    buffer (L2 -> SM when it fits in L2). See include/sivf.h."""
+    lib = load()
+    gbs, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib, None, lib.sivf_measure_read_bandwidth(buf, nbytes, passes, stream, ctypes.byref(gbs),
+                                                      ctypes.byref(ms)))
+    return gbs.value, ms.value
+
+
 def sivf_destroy(ctx: int) -> None:
     if ctx:
         load().sivf_destroy(ctx)
@@ -227,7 +243,8 @@ class SIVF:
     def __init__(self, row_ptr, idx, val, D: int, k: int, init_ids, precision: str = "fp32", icp=True,
                  threads: int = 0, ctas_per_sm: int = 0, mem_cap_bytes: int = 0, stream=None, use_graph: bool = False,
                  autotune: bool = False, score_buffer: str = "auto", inputs_on_host: bool = False,
-                 update_mode: str = "auto"):
+                 update_mode: str = "auto", checked: bool = False, dense_max_bytes: int = 0,
+                 dense_min_fraction: float = 0.0):
         import numpy as np
         import torch
 
@@ -269,7 +286,8 @@ class SIVF:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         cfg = sivf_config(PRECISIONS[precision], icp_mode(icp), int(threads), int(ctas_per_sm), int(mem_cap_bytes),
                           int(bool(use_graph)), int(bool(autotune)), SCORE_BUFFERS[score_buffer],
-                          UPDATE_MODES[update_mode], int(bool(inputs_on_host)))
+                          UPDATE_MODES[update_mode], int(bool(inputs_on_host)), int(bool(checked)),
+                          int(dense_max_bytes), float(dense_min_fraction))
         self.ctx = sivf_init(cfg, self.N, self.D, self.k, rp_p, ix_p, vl_p, ini.ctypes.data, self.stream.cuda_stream)
 
     def close(self):
@@ -401,7 +419,7 @@ class SIVFBatch:
 
     def __init__(self, corpora, ks, init_ids, precision: str = "fp32", icp=True, threads: int = 0,
                  ctas_per_sm: int = 0, use_graph: bool = False, autotune: bool = False, score_buffer: str = "auto",
-                 update_mode: str = "auto"):
+                 update_mode: str = "auto", dense_max_bytes: int = 0, dense_min_fraction: float = 0.0):
         import numpy as np
         import torch
 
@@ -427,7 +445,7 @@ class SIVFBatch:
         self.ks = [int(k) for k in ks]
         cfg = sivf_config(PRECISIONS[precision], icp_mode(icp), int(threads), int(ctas_per_sm), 0,
                           int(bool(use_graph)), int(bool(autotune)), SCORE_BUFFERS[score_buffer],
-                          UPDATE_MODES[update_mode])
+                          UPDATE_MODES[update_mode], 0, 0, int(dense_max_bytes), float(dense_min_fraction))
         self.ctx = sivf_batch_init(cfg, descs)
         self._keep = None  # the library copied the corpora
 

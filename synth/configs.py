@@ -46,6 +46,9 @@ CONFIGS = {
     "c3": Workload("c3", 1_000_000, 140_000, 1.1, 4.2, 0.8, 5, 3000, 10_000, 50, "bf16", 3),
     # C5: large single instance, BF16 postings
     "c5": Workload("c5", 8_000_000, 140_000, 1.1, _mu_for_mean(60.0, 0.8), 0.8, 5, 3000, 20_000, 20, "bf16", 5),
+    # the C5 regime scaled to 1/16 of its objects (k = 20,000 kept; 30M nnz,
+    # a 0.25 GB CSR, still larger than L2): the case kernel profiles capture
+    "c5s": Workload("c5s", 500_000, 140_000, 1.1, _mu_for_mean(60.0, 0.8), 0.8, 5, 3000, 20_000, 20, "bf16", 55),
 }
 
 

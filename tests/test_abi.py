@@ -206,3 +206,19 @@ def test_binding_checks_array_sizes_before_the_library_reads_them():
     for out in (torch.zeros(4, dtype=torch.int32), torch.zeros(4, dtype=torch.int64), [0, 0, 0, 0]):
         with pytest.raises(ValueError):
             S.SIVF.labels_device(Ctx(), out=out)
+
+
+def test_noalloc_rejects_sizes_beyond_its_limits_on_the_host():
+    """The allocation-free build checks k, D, n_entries and the pointers on the
+    host before any CUDA call (no GPU needed); the device arrays are never
+    read (the pointers below are not even valid)."""
+    from paper_2103_16141_gb300 import sivf as S
+    lib = S.load()
+    INVALID = S.SIVF_ERR_INVALID_ARG
+    limits = dict(k=1 << 20, D=1 << 18, n=1 << 20)
+    for k, D, n in [(limits["k"] + 1, 100, 10), (4, limits["D"] + 1, 10), (4, 100, limits["n"] + 1),
+                    (0, 100, 10), (4, 0, 10), (4, 100, -1)]:
+        assert lib.sivf_build_inverted_file_noalloc(k, D, n, 1, 1, 1, 1, 1, 1, 1, 1, None) == INVALID, (k, D, n)
+    # NULL pointers
+    assert lib.sivf_build_inverted_file_noalloc(4, 100, 10, None, 1, 1, 1, 1, 1, 1, 1, None) == INVALID
+    assert lib.sivf_build_inverted_file_noalloc(4, 100, 10, 1, None, 1, 1, 1, 1, 1, 1, None) == INVALID
