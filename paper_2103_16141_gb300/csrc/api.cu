@@ -695,6 +695,7 @@ sivf_status graph_loop(sivf_ctx *c, int32_t max_total, std::vector<int32_t> &don
     API_CUDA(c, cudaMemcpyAsync(c->objf_dev, c->objf_pin, sizeof(double) * ni, cudaMemcpyHostToDevice, s), "copy");
     const int32_t iter0 = c->iter;
     API_CUDA(c, cudaGraphLaunch(c->graph_exec, s), "graph launch");
+    c->canon_stale = true;  // the replayed updates rebuilt the file
     API_CUDA(c, cudaMemcpyAsync(lp, c->loop_dev, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, s), "copy");
     API_CUDA(c, cudaMemcpyAsync(lp + 4, c->done_dev, sizeof(int32_t) * ni, cudaMemcpyDeviceToHost, s), "copy");
     API_CUDA(c, cudaMemcpyAsync(c->objf_pin, c->objf_dev, sizeof(double) * ni, cudaMemcpyDeviceToHost, s), "copy");
@@ -860,6 +861,7 @@ sivf_status sivf_get_inverted_file(sivf_ctx *c, int64_t *off, int32_t *mf0, int3
     if (!c) return SIVF_ERR_INVALID_ARG;
     if (c->latched) return SIVF_ERR_STATE;
     if (!off || !mf0) return fail(c, SIVF_ERR_INVALID_ARG, "off/mf0 is NULL");
+    API_CUDA(c, build_canonical_if(c), "canonical inverted file");
     API_CUDA(c, cudaMemcpyAsync(off, c->if_off, sizeof(int64_t) * (c->D + 1), cudaMemcpyDeviceToHost, c->stream),
              "copy");
     API_CUDA(c, cudaMemcpyAsync(mf0, c->if_mf0, sizeof(int32_t) * c->D, cudaMemcpyDeviceToHost, c->stream), "copy");

@@ -353,74 +353,89 @@ __device__ __forceinline__ void rho_zero(uint32_t *p) {
     else *p = 0u;
 }
 
-// Dense head rows: 8 consecutive entries (one 16-byte load for BF16/FP16, two
-// for FP32) decoded to FP32. FP16 rows hold u * 2^14 (the scale is folded into
-// the object value by the caller).
+// Dense head rows: 8 consecutive entries of a row (one 16-byte load for
+// BF16/FP16, two for FP32), loaded raw and decoded to FP32 afterwards, so
+// that the loads of several rows can be in flight together. FP16 rows hold
+// u * 2^14 (the scale is folded into the object value by the caller).
 template <int PREC>
-__device__ __forceinline__ void load_dense8(const void *dense, int64_t e, float u[8]) {
+struct Raw8 {
+    uint4 w[PREC == SIVF_FP32 ? 2 : 1];
+};
+
+template <int PREC>
+__device__ __forceinline__ Raw8<PREC> load_raw8(const void *dense, int64_t e) {
+    Raw8<PREC> r;
     if constexpr (PREC == SIVF_FP32) {
-        const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float *>(dense) + e);
-        const float4 a = __ldg(p), b = __ldg(p + 1);
-        u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
-        u[4] = b.x; u[5] = b.y; u[6] = b.z; u[7] = b.w;
+        const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const float *>(dense) + e);
+        r.w[0] = __ldg(p);
+        r.w[1] = __ldg(p + 1);
     } else {
-        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(static_cast<const uint16_t *>(dense) + e));
-        const unsigned ws[4] = {w.x, w.y, w.z, w.w};
+        r.w[0] = __ldg(reinterpret_cast<const uint4 *>(static_cast<const uint16_t *>(dense) + e));
+    }
+    return r;
+}
+
+// acc[m] += vs * u[m] for the 8 entries, in entry order
+template <int PREC>
+__device__ __forceinline__ void fma_raw8(const Raw8<PREC> &r, float vs, float acc[8]) {
+    if constexpr (PREC == SIVF_FP32) {
+        const unsigned ws[8] = {r.w[0].x, r.w[0].y, r.w[0].z, r.w[0].w, r.w[1].x, r.w[1].y, r.w[1].z, r.w[1].w};
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[m] = fmaf(vs, __uint_as_float(ws[m]), acc[m]);
+    } else {
+        const unsigned ws[4] = {r.w[0].x, r.w[0].y, r.w[0].z, r.w[0].w};
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
+            float lo, hi;
             if constexpr (PREC == SIVF_BF16) {
-                u[2 * m] = __uint_as_float(ws[m] << 16);
-                u[2 * m + 1] = __uint_as_float(ws[m] & 0xFFFF0000u);
+                lo = __uint_as_float(ws[m] << 16);
+                hi = __uint_as_float(ws[m] & 0xFFFF0000u);
             } else {
                 const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&ws[m]));
-                u[2 * m] = f.x;
-                u[2 * m + 1] = f.y;
+                lo = f.x;
+                hi = f.y;
             }
+            acc[2 * m] = fmaf(vs, lo, acc[2 * m]);
+            acc[2 * m + 1] = fmaf(vs, hi, acc[2 * m + 1]);
         }
     }
 }
 
-// Dense phase of one staged chunk: every thread owns 8-entry groups of scan
-// positions (group c * T + tid of each pass) and accumulates, in FP32
+// Dense phase of one staged chunk: thread tid owns the 8 scan positions
+// base + 8 tid of each pass (8 T positions per pass) and accumulates, in FP32
 // registers, v * u over the chunk's dense terms in staging order; each
 // position's partial sum is then added to the score as one fixed-point value.
-// Positions [0, npos) are covered: the moving clusters for a front scan, all
-// of the instance's clusters otherwise. A position's sum depends only on the
-// chunk's terms, never on which thread or pass covers it, so front and full
-// scans give the same scores.
-constexpr int DENSE_NCH = 2;  // 8-entry groups per thread and pass
+// The loads of DENSE_U consecutive terms are issued together (about 128 bytes
+// in flight per thread), their multiply-adds follow in term order. Positions
+// [0, npos) are covered: the moving clusters for a front scan, all of the
+// instance's clusters otherwise. A position's sum depends only on the chunk's
+// terms, never on which thread or pass covers it, so front and full scans give
+// the same scores.
 template <int T, int PREC, bool GRHO>
 __device__ __forceinline__ void dense_chunk(const AssignParams &P, uint32_t *rho, const int2 *s_dense, int nd,
                                             int npos) {
-    constexpr int PER_PASS = 8 * DENSE_NCH * T;
-    for (int base = 0; base < npos; base += PER_PASS) {
-        float acc[DENSE_NCH][8];
+    constexpr int U = PREC == SIVF_FP32 ? 4 : 8;
+    for (int base = 0; base < npos; base += 8 * T) {
+        const int p = base + 8 * (int)threadIdx.x;
+        if (p >= npos) continue;  // rows are padded to multiples of 8: a load at p < npos stays in the row
+        float acc[8];
 #pragma unroll
-        for (int c = 0; c < DENSE_NCH; ++c)
+        for (int m = 0; m < 8; ++m) acc[m] = 0.f;
+        int d = 0;
+        for (; d + U <= nd; d += U) {
+            Raw8<PREC> r[U];
 #pragma unroll
-            for (int m = 0; m < 8; ++m) acc[c][m] = 0.f;
-        for (int d = 0; d < nd; ++d) {
-            const int2 e = s_dense[d];
-            const float vs = __int_as_float(e.y);
-            const int64_t row = (int64_t)e.x * 8;
+            for (int q = 0; q < U; ++q) r[q] = load_raw8<PREC>(P.dense, (int64_t)s_dense[d + q].x * 8 + p);
 #pragma unroll
-            for (int c = 0; c < DENSE_NCH; ++c) {
-                const int p = base + (c * T + (int)threadIdx.x) * 8;
-                if (p < npos) {  // rows are padded to multiples of 8: the load stays in the row
-                    float u[8];
-                    load_dense8<PREC>(P.dense, row + p, u);
-#pragma unroll
-                    for (int m = 0; m < 8; ++m) acc[c][m] = fmaf(vs, u[m], acc[c][m]);
-                }
-            }
+            for (int q = 0; q < U; ++q) fma_raw8<PREC>(r[q], __int_as_float(s_dense[d + q].y), acc);
+        }
+        for (; d < nd; ++d) {
+            const Raw8<PREC> r = load_raw8<PREC>(P.dense, (int64_t)s_dense[d].x * 8 + p);
+            fma_raw8<PREC>(r, __int_as_float(s_dense[d].y), acc);
         }
 #pragma unroll
-        for (int c = 0; c < DENSE_NCH; ++c) {
-            const int p = base + (c * T + (int)threadIdx.x) * 8;
-#pragma unroll
-            for (int m = 0; m < 8; ++m)
-                if (p + m < npos && acc[c][m] > 0.f) atomicAdd(rho + p + m, __float2uint_ru(acc[c][m]));
-        }
+        for (int m = 0; m < 8; ++m)
+            if (p + m < npos && acc[m] > 0.f) atomicAdd(rho + p + m, __float2uint_ru(acc[m]));
     }
 }
 

@@ -11,15 +11,18 @@
 //   centroids (x2)        coff int64[k+1], cterm int32[cap], cval f32[cap], cclu int32[cap]
 //                                        cluster-major FP32 master copy, ascending terms
 //   snorm                 f64[k]        ||s_j|| of the sum behind each centroid
-//   inverted file         if_off int64[D+1], if_mf0 int32[D], if_cid int32[cap],
+//   inverted file         if_off int64[D+1], if_mf0 int32[D]; if_cid int32[cap],
 //                                        if_val f32[cap]: canonical order (front ids
-//                                        ascending, then back ids ascending)
+//                                        ascending, then back ids ascending), built
+//                                        on demand for the getters
 //   scan copy of the file sc_off int64[D+1]: each list starts at a multiple of 4
 //                                        entries; a list's full 128-entry blocks are
 //                                        stored transposed (entry 32m + l of a block at
 //                                        block position 4l + m), so that lane l reads
 //                                        entries l, 32+l, 64+l, 96+l with one vector
-//                                        load; the ragged tail keeps canonical order.
+//                                        load; the ragged tail keeps list order. Inside
+//                                        a segment the postings are in the order the
+//                                        build's atomic cursor handed out.
 //                                        Arrays (scan positions): sc_id16 u16 or
 //                                        sc_id32 int32, plus sc_val f32 (FP32), or
 //                                        sc_pack u32 = id << 16 | bf16/fp16 value
@@ -150,6 +153,7 @@ struct sivf_ctx {
     int32_t *if_cid = nullptr;
     float *if_val = nullptr;
     int64_t if_nnz = 0;
+    bool canon_stale = true;  // if_cid / if_val predate the last inverted-file build
     // scan copy (tiled layout, local ids); which arrays exist depends on the
     // id width (16 bits when every instance has k <= 65536) and the precision
     int64_t *sc_off = nullptr;
@@ -272,6 +276,7 @@ cudaError_t enqueue_update(sivf_ctx *c, bool timing);
 // ---- update.cu ----
 cudaError_t run_update(sivf_ctx *c);
 cudaError_t build_inverted_file(sivf_ctx *c);
+cudaError_t build_canonical_if(sivf_ctx *c);
 cudaError_t validate_csr(sivf_ctx *c, int *bad);
 cudaError_t init_centroids(sivf_ctx *c, const int32_t *init_ids_dev);
 cudaError_t set_labels_dev(sivf_ctx *c, const int32_t *src_dev);

@@ -689,85 +689,6 @@ __global__ void k_if_fill(const int64_t *n_dev, int64_t cap, const uint32_t *ord
     }
 }
 
-// Scan copy of the file, one warp per segment (the front or the back of a
-// list) of every term without a dense row. The copy holds each posting's scan
-// position (the index of its score). Inside a segment the postings are
-// reordered so that 32 consecutive ones fall on distinct shared-memory banks
-// of the score vector (bank = position mod 32) as far as the segment allows: by rank among the segment's
-// postings of the same bank, then by bank. Consecutive ranks then cover every
-// bank once while all banks last, and a window of 32 that straddles two such
-// ranks still does. The order inside a part does not change any score (each
-// posting is one integer add). The reordered postings are then stored at
-// their tiled positions with local ids and the scan's value encoding.
-constexpr int SC_COPY_THREADS = 256;
-__global__ void __launch_bounds__(SC_COPY_THREADS) k_if_scan_copy(
-    int32_t D, const int64_t *if_off, const int32_t *if_mf0, const int64_t *sc_off, const int32_t *if_cid,
-    const float *if_val, const int32_t *clu_pos, const int32_t *dense_row, int prec, uint16_t *sc_id16,
-    int32_t *sc_id32, float *sc_val, uint32_t *sc_pack, uint16_t *sc_lp) {
-    __shared__ int s_cnt[SC_COPY_THREADS / 32][32];
-    __shared__ int s_run[SC_COPY_THREADS / 32][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned below = (1u << lane) - 1u;
-    const int64_t nw = ((int64_t)gridDim.x * SC_COPY_THREADS) >> 5;
-    for (int64_t seg = (blockIdx.x * (int64_t)SC_COPY_THREADS + threadIdx.x) >> 5; seg < 2 * (int64_t)D; seg += nw) {
-        const int t = (int)(seg >> 1);
-        if (dense_row[t] >= 0) continue;  // read from its dense row instead
-        const int64_t o = if_off[t];
-        const int L = (int)(if_off[t + 1] - o), m0 = if_mf0[t];
-        const int s0 = (seg & 1) ? m0 : 0, n = (seg & 1) ? L - m0 : m0;
-        if (n <= 0) continue;
-        s_cnt[w][lane] = 0;
-        s_run[w][lane] = 0;
-        __syncwarp();
-        for (int c0 = 0; c0 < n; c0 += 32) {  // postings per bank
-            if (c0 + lane < n) {
-                const int32_t j = if_cid[o + s0 + c0 + lane];
-                atomicAdd(&s_cnt[w][clu_pos[j] & 31], 1);
-            }
-        }
-        __syncwarp();
-        const int cnt = s_cnt[w][lane];  // lane b: postings of bank b
-        const int64_t base = sc_off[t];
-        for (int c0 = 0; c0 < n; c0 += 32) {
-            const bool ok = c0 + lane < n;
-            const int64_t q = o + s0 + c0 + lane;
-            const int32_t j = ok ? if_cid[q] : 0;
-            const uint32_t jl = ok ? (uint32_t)clu_pos[j] : 0u;  // the posting's scan position
-            const int bank = (int)(jl & 31);
-            const unsigned peers = __match_any_sync(0xffffffffu, ok ? bank : 32 + lane);
-            const int rank = (ok ? s_run[w][bank] : 0) + __popc(peers & below);
-            __syncwarp();
-            if (ok && (peers & below) == 0) s_run[w][bank] += __popc(peers);  // group leader
-            __syncwarp();
-            // destination in the segment: postings of lower rank, then lower banks of equal rank
-            int d = 0;
-#pragma unroll 8
-            for (int b = 0; b < 32; ++b) {
-                const int cb = __shfl_sync(0xffffffffu, cnt, b);
-                d += min(cb, rank) + ((b < bank && cb > rank) ? 1 : 0);
-            }
-            if (!ok) continue;
-            const int64_t pos = base + tiled_pos(s0 + d, L);  // s0 + d: index in the list
-            const float u = if_val[q];
-            if (sc_id16) sc_id16[pos] = (uint16_t)jl;
-            if (sc_id32) sc_id32[pos] = (int32_t)jl;
-            if (prec == SIVF_FP32) {
-                sc_val[pos] = u;
-                continue;
-            }
-            unsigned short lp;
-            if (prec == SIVF_BF16) {
-                lp = __bfloat16_as_ushort(__float2bfloat16_rn(u));
-            } else {
-                lp = __half_as_ushort(__float2half_rn(u * FP16_SCALE));
-                if (lp == 0 && u > 0.0f) lp = 1;  // keep every posting strictly positive
-            }
-            if (sc_pack) sc_pack[pos] = (jl << 16) | (uint32_t)lp;
-            else sc_lp[pos] = lp;
-        }
-    }
-}
-
 // ---------------- scan order and dense head rows ----------------
 
 // Scan position of every cluster: within its instance, the moving clusters of
@@ -880,28 +801,60 @@ __global__ void k_dense_zero(const int64_t *used8, int esize, uint4 *dense) {
         dense[q] = make_uint4(0u, 0u, 0u, 0u);
 }
 
-// One warp per dense term: every posting's value at its cluster's position.
-__global__ void k_dense_fill(int32_t D, const int32_t *dense_row, const int64_t *if_off, const int32_t *if_cid,
-                             const float *if_val, const int32_t *clu_pos, int prec, void *dense) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < D; t += nw) {
+// 16-bit stored value of a posting: BF16 (nearest, ties to even), or FP16 of
+// u * 2^14 kept strictly positive
+__device__ __forceinline__ uint16_t encode_lp(float u, int prec) {
+    if (prec == SIVF_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(u));
+    unsigned short h = __half_as_ushort(__float2half_rn(u * FP16_SCALE));
+    if (h == 0 && u > 0.0f) h = 1;
+    return h;
+}
+
+// per (term, part) posting counts of the current centroids
+__global__ void k_if_count(const int64_t *n_dev, int64_t cap, const int32_t *cterm, const int32_t *cclu,
+                           const uint8_t *lam, int structured, uint32_t *cnt2) {
+    const int64_t n = min(*n_dev, cap);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(cnt2 + (((uint32_t)cterm[e] << 1) | (uint32_t)(structured && lam[cclu[e]] ? 1 : 0)), 1u);
+}
+
+// The scan structures read by the assignment, straight from the cluster-major
+// centroid entries (one pass, no sort): an entry of a term with a dense row
+// goes to the row at its cluster's scan position; any other entry takes the
+// next free slot of its term's front (moving cluster) or back (invariant
+// cluster) in the scan copy, stored at the slot's tiled position with the
+// cluster's scan position as its id. The order of the postings inside a
+// segment follows the atomic cursor; no score depends on it (each posting is
+// one integer add).
+__global__ void k_scan_fill(const int64_t *n_dev, int64_t cap, const int32_t *cterm, const int32_t *cclu,
+                            const float *cval, const uint8_t *lam, int structured, const int32_t *clu_pos,
+                            const int32_t *dense_row, const int64_t *if_off, const int32_t *if_mf0,
+                            const int64_t *sc_off, uint32_t *cursor, int prec, void *dense, uint16_t *sc_id16,
+                            int32_t *sc_id32, float *sc_val, uint32_t *sc_pack, uint16_t *sc_lp) {
+    const int64_t n = min(*n_dev, cap);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t t = cterm[e], j = cclu[e];
+        const float u = cval[e];
+        const uint32_t p = (uint32_t)clu_pos[j];
         const int32_t r = dense_row[t];
-        if (r < 0) continue;
-        const int64_t base = (int64_t)r * 8;
-        for (int64_t q = if_off[t] + lane; q < if_off[t + 1]; q += 32) {
-            const int64_t e = base + clu_pos[if_cid[q]];
-            const float u = if_val[q];
-            if (prec == SIVF_FP32) {
-                static_cast<float *>(dense)[e] = u;
-            } else if (prec == SIVF_BF16) {
-                static_cast<uint16_t *>(dense)[e] = __bfloat16_as_ushort(__float2bfloat16_rn(u));
-            } else {
-                unsigned short h = __half_as_ushort(__float2half_rn(u * FP16_SCALE));
-                if (h == 0 && u > 0.0f) h = 1;  // keep every stored value strictly positive
-                static_cast<uint16_t *>(dense)[e] = h;
-            }
+        if (r >= 0) {
+            const int64_t d = (int64_t)r * 8 + p;
+            if (prec == SIVF_FP32) static_cast<float *>(dense)[d] = u;
+            else static_cast<uint16_t *>(dense)[d] = encode_lp(u, prec);
+            continue;
         }
+        const uint32_t part = (structured && lam[j]) ? 1u : 0u;
+        const int64_t slot = (int64_t)atomicAdd(cursor + (((uint32_t)t << 1) | part), 1u) + (part ? if_mf0[t] : 0);
+        const int64_t pos = sc_off[t] + tiled_pos(slot, if_off[t + 1] - if_off[t]);
+        if (sc_id16) sc_id16[pos] = (uint16_t)p;
+        if (sc_id32) sc_id32[pos] = (int32_t)p;
+        if (prec == SIVF_FP32) {
+            sc_val[pos] = u;
+            continue;
+        }
+        const uint16_t lp = encode_lp(u, prec);
+        if (sc_pack) sc_pack[pos] = (p << 16) | (uint32_t)lp;
+        else sc_lp[pos] = lp;
     }
 }
 
@@ -991,8 +944,11 @@ cudaError_t reseed_dev(sivf_ctx *c, const int32_t *init_ids_dev) {
     return cudaSuccess;
 }
 
-// Structured inverted file of the current centroids (count in coff[k], on the
-// device) with the current lambda. No host synchronisation.
+// Scan structures of the structured inverted file of the current centroids
+// (count in coff[k], on the device) with the current lambda: list offsets and
+// front lengths, the scan order, the dense head rows and the sparse scan copy.
+// No host synchronisation. The canonical file (ascending ids in each part,
+// for the getters) is built on demand by build_canonical_if.
 cudaError_t build_inverted_file(sivf_ctx *c) {
     const int64_t cap = c->cap_c;
     const int cur = c->cur;
@@ -1007,14 +963,12 @@ cudaError_t build_inverted_file(sivf_ctx *c) {
     int64_t *base8 = ws.take<int64_t>((size_t)D + 1);
     unsigned long long *hist = ws.take<unsigned long long>(DENSE_BINS + 1);
     int64_t *total = ws.take<int64_t>(3);
-    uint32_t *k0 = ws.take<uint32_t>((size_t)cap + 1), *v0 = ws.take<uint32_t>((size_t)cap + 1);
-    uint32_t *k1 = ws.take<uint32_t>((size_t)cap + 1), *v1 = ws.take<uint32_t>((size_t)cap + 1);
-    if (!cnt2 || !len || !slen || !w8 || !base8 || !hist || !total || !k0 || !v0 || !k1 || !v1)
-        return cudaErrorMemoryAllocation;
+    if (!cnt2 || !len || !slen || !w8 || !base8 || !hist || !total) return cudaErrorMemoryAllocation;
     cudaStream_t s = c->stream;
     const bool cb = c->cfg.icp == 2;
+    c->canon_stale = true;
     SIVF_CUDA_TRY(cudaMemsetAsync(cnt2, 0, sizeof(uint32_t) * 2 * D, s));
-    k_if_keys<<<blocks_gs(cap), TPB, 0, s>>>(n_dev, cap, c->cterm[cur], c->cclu, c->lam, cb ? 0 : 1, k0, v0, cnt2);
+    k_if_count<<<blocks_gs(cap), TPB, 0, s>>>(n_dev, cap, c->cterm[cur], c->cclu, c->lam, cb ? 0 : 1, cnt2);
     k_if_lens<<<blocks_for(D), TPB, 0, s>>>(D, cnt2, len, slen, c->if_mf0);
     // scan order of lambda^[r] (mov_list and mov_beg were computed from it)
     k_positions<<<blocks_gs(c->k), TPB, 0, s>>>(c->k, c->n_inst, c->inst_k, c->lam, c->mov_list, c->mov_beg,
@@ -1045,25 +999,55 @@ cudaError_t build_inverted_file(sivf_ctx *c) {
     SIVF_CUDA_TRY(cudaMemsetAsync(&c->ctr->dense_terms, 0, sizeof(long long), s));
     k_dense_rows<<<blocks_gs(D), TPB, 0, s>>>(D, w8, base8, c->dense_row, c->ctr);
     note_launch();
-    bool alt = false;
-    SIVF_CUDA_TRY(radix_sort_pairs_dev(k0, v0, k1, v1, cap, n_dev, c->bits_t + 1, &alt, ws, s));
-    k_if_fill<<<blocks_gs(cap), TPB, 0, s>>>(n_dev, cap, alt ? v1 : v0, c->cclu, c->cval[cur], c->if_cid,
-                                              c->if_val);
-    k_if_scan_copy<<<blocks_gs((int64_t)2 * D * 32, SC_COPY_THREADS), SC_COPY_THREADS, 0, s>>>(
-        D, c->if_off, c->if_mf0, c->sc_off, c->if_cid, c->if_val, c->clu_pos, c->dense_row, (int)c->cfg.prec,
-        c->sc_id16, c->sc_id32, c->sc_val, c->sc_pack, c->sc_lp);
-    note_launch(2);
     if (dense) {
         const int esize = c->cfg.prec == SIVF_FP32 ? 4 : 2;
         k_dense_zero<<<blocks_gs(c->cap_dense * esize / 16), TPB, 0, s>>>(total + 2, esize,
                                                                             static_cast<uint4 *>(c->dense_val));
-        k_dense_fill<<<blocks_gs((int64_t)D * 32), TPB, 0, s>>>(D, c->dense_row, c->if_off, c->if_cid, c->if_val,
-                                                                  c->clu_pos, (int)c->cfg.prec, c->dense_val);
-        note_launch(2);
+        note_launch();
     }
+    // the counts are consumed: the same array now hands out the slots
+    SIVF_CUDA_TRY(cudaMemsetAsync(cnt2, 0, sizeof(uint32_t) * 2 * D, s));
+    k_scan_fill<<<blocks_gs(cap), TPB, 0, s>>>(n_dev, cap, c->cterm[cur], c->cclu, c->cval[cur], c->lam, cb ? 0 : 1,
+                                                c->clu_pos, c->dense_row, c->if_off, c->if_mf0, c->sc_off, cnt2,
+                                                (int)c->cfg.prec, c->dense_val, c->sc_id16, c->sc_id32, c->sc_val,
+                                                c->sc_pack, c->sc_lp);
+    note_launch();
     SIVF_CUDA_TRY(cudaMemcpyAsync(&c->ctr->dense_used, total + 2, sizeof(long long), cudaMemcpyDeviceToDevice, s));
     SIVF_CUDA_TRY(cudaGetLastError());
     ws.used = mark;
+    return cudaSuccess;
+}
+
+// The canonical structured inverted file of the current centroids and lambda
+// (Algorithm 5: for every term, the moving centroids first and the invariant
+// ones after, ascending ids in each part) in if_cid / if_val, with the offsets
+// and front lengths of the last build: a stable radix sort of the centroid
+// entries by (term, part). Used by the getters only; synchronises the stream.
+cudaError_t build_canonical_if(sivf_ctx *c) {
+    if (!c->canon_stale) return cudaSuccess;
+    const int64_t cap = c->cap_c;
+    const int cur = c->cur;
+    const int64_t *n_dev = c->coff[cur] + c->k;
+    Workspace &ws = c->ws;
+    ws.reset();
+    uint32_t *cnt2 = ws.take<uint32_t>((size_t)2 * c->D);
+    uint32_t *k0 = ws.take<uint32_t>((size_t)cap + 1), *v0 = ws.take<uint32_t>((size_t)cap + 1);
+    uint32_t *k1 = ws.take<uint32_t>((size_t)cap + 1), *v1 = ws.take<uint32_t>((size_t)cap + 1);
+    if (!cnt2 || !k0 || !v0 || !k1 || !v1) return cudaErrorMemoryAllocation;
+    cudaStream_t s = c->stream;
+    SIVF_CUDA_TRY(cudaMemsetAsync(cnt2, 0, sizeof(uint32_t) * 2 * c->D, s));
+    k_if_keys<<<blocks_gs(cap), TPB, 0, s>>>(n_dev, cap, c->cterm[cur], c->cclu, c->lam, c->cfg.icp == 2 ? 0 : 1, k0,
+                                              v0, cnt2);
+    note_launch();
+    bool alt = false;
+    SIVF_CUDA_TRY(radix_sort_pairs_dev(k0, v0, k1, v1, cap, n_dev, c->bits_t + 1, &alt, ws, s));
+    k_if_fill<<<blocks_gs(cap), TPB, 0, s>>>(n_dev, cap, alt ? v1 : v0, c->cclu, c->cval[cur], c->if_cid,
+                                              c->if_val);
+    note_launch();
+    SIVF_CUDA_TRY(cudaGetLastError());
+    SIVF_CUDA_TRY(cudaStreamSynchronize(s));
+    ws.reset();
+    c->canon_stale = false;
     return cudaSuccess;
 }
 
