@@ -473,11 +473,13 @@ def file_bytes(g, prec, k):
 
 
 def trajectory(per):
-    return [(int(p["changed"]), int(p["postings"]), int(p.get("dense_entries", 0)), int(p["filtered"]),
-             int(p["n_moving"])) for p in per]
+    """The method-level counts of each iteration (independent of the posting
+    precision and of which lists are held in dense rows)."""
+    return [(int(p["changed"]), int(p["postings"]), int(p["filtered"]), int(p["simcalc"]), int(p["n_moving"]))
+            for p in per]
 
 
-def run_e2e(c, csr, w, ini, prec, args, stream, world):
+def run_e2e(c, csr, w, ini, prec, args, stream, world, local):
     """The same window through the C ABI with host buffers: every timed step
     copies the CSR from pinned host memory into the device buffers the context
     reads, runs one Lloyd iteration and reads the labels back."""
@@ -493,6 +495,8 @@ def run_e2e(c, csr, w, ini, prec, args, stream, world):
         for _ in range(args.warmup):
             path.step()
         E = args.e2e_steps if args.e2e_steps > 0 else args.steps
+        sampler = ClockSampler(local)
+        sampler.start()
         barrier_and_sync(world)
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
@@ -504,11 +508,12 @@ def run_e2e(c, csr, w, ini, prec, args, stream, world):
                 S.sivf_get_labels(path.g.ctx, lab_h.data_ptr(), False)
         barrier_and_sync(world)
         dt = max_over_ranks(time.perf_counter() - t0, world)
+        clocks = sampler.stop()
     finally:
         path.close()
     h2d = rp_h.numel() * 8 + ix_h.numel() * 4 + vl_h.numel() * 4
     return {"value": sum_over_ranks(float(w.N * E), world) / dt, "unit": "objects/s", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": w.N * 4, "steps": E,
+            "d2h_bytes_per_step": w.N * 4, "steps": E, "clocks": clocks,
             "window": f"iterations {args.warmup + 1}-{args.warmup + E}, a separate run from the same seeds"
                       + (" (the timed window)" if E == args.steps else "")}
 
@@ -617,22 +622,25 @@ def main():
     vs_fp32 = None
     if not args.no_fp32 and prec != "fp32":
         p32 = Path(c, csr, w, ini, "fp32", args)
-        ms32, per32, _, _ = timed_window(p32, args, stream, world)
+        ms32, per32, _, clocks32 = timed_window(p32, args, stream, world, ClockSampler(local))
         sb32, db32 = file_bytes(p32.g, "fp32", w.k)
         lab32 = p32.g.labels()
         p32.close()
         _, ms32_max = replica_throughput(w.N * args.steps, ms32, world)
-        same = trajectory(per) == trajectory(per32) and bool(np.array_equal(lab_end, lab32))
+        same_counts = trajectory(per) == trajectory(per32)
+        same_labels = bool(np.array_equal(lab_end, lab32))
         vs_fp32 = {"sec_per_iter": ms_max / 1e3 / args.steps, "fp32_sec_per_iter": ms32_max / 1e3 / args.steps,
                    "speedup": ms32_max / ms_max, "precision": prec,
                    "fp32_roofline": roofline(per32, w, c.nnz, "fp32", peaks, hbm_peak, sb32, db32),
-                   "labels_identical_every_iteration": same,
+                   "same_counts_every_iteration": same_counts, "same_final_labels": same_labels,
+                   "fp32_clocks": clocks32,
                    "equal_accuracy": "both paths re-score every object whose top-2 margin lies inside their "
                                      "derived error bound exactly (FP64 from the FP32 master centroids), so both "
-                                     "give the argmax of the exact scores: the per-iteration changed/posting/"
-                                     "filtered/moving counts and the final labels are compared"}
+                                     "give the argmax of the exact scores: the changed, posting, filtered, "
+                                     "similarity and moving counts of every iteration and the labels after the "
+                                     "window are compared"}
 
-    e2e = None if args.no_e2e else run_e2e(c, csr, w, ini, prec, args, stream, world)
+    e2e = None if args.no_e2e else run_e2e(c, csr, w, ini, prec, args, stream, world, local)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, c, ini, args.icp)

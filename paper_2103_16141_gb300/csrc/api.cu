@@ -53,7 +53,8 @@ void free_all(sivf_ctx *c) {
                     c->ctr, c->obj_dev, c->ws.base, c->inst_obj, c->inst_k, c->mov_beg, c->clu_koff,
                     c->inst_changed, c->own_row_ptr, c->own_idx, c->own_val, c->clu_doff,
                     c->loop_dev, c->done_dev, c->objf_dev, c->grho, c->acc, c->acc_off, c->acc_lab,
-                    c->clu_pos, c->pos_clu, c->dense_row, c->dense_val, c->inst_d, c->dense_thr};
+                    c->clu_pos, c->pos_clu, c->dense_row, c->dense_val, c->inst_d, c->dense_thr,
+                    c->heavy_ids, c->light_ids};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     destroy_loop_graph(c);
@@ -196,6 +197,8 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
     const int64_t capc = c->cap_c;
     const int32_t ni = c->n_inst;
     INIT_CUDA(dmalloc(c, &c->labels, N), "alloc");
+    INIT_CUDA(dmalloc(c, &c->heavy_ids, N), "alloc");
+    INIT_CUDA(dmalloc(c, &c->light_ids, N), "alloc");
     INIT_CUDA(dmalloc(c, &c->labels_prev, N), "alloc");
     INIT_CUDA(dmalloc(c, &c->own, N), "alloc");
     INIT_CUDA(dmalloc(c, &c->sumv, N), "alloc");

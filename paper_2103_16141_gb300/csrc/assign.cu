@@ -68,6 +68,9 @@ struct AssignParams {
     const int32_t *pos_clu;    // instance cluster offset + scan position -> local id
     const int32_t *dense_row;  // [D]: first entry / 8 of the term's dense row, -1 = sparse
     const void *dense;         // dense rows: u16 (BF16, FP16 x 2^14) or f32
+    const int32_t *heavy_ids;  // objects of the CTA-per-object kernel (ctr->n_heavy of them)
+    const int32_t *light_ids;  // objects of the warp-per-object kernel (ctr->n_light of them)
+    int chunk;                 // terms staged per chunk by the CTA kernel (its block size)
     uint32_t *grho;            // global score vectors, one kmax slab per CTA (global score-buffer variant)
     const int64_t *coff;
     const int32_t *cterm;
@@ -494,11 +497,12 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
     unsigned long long c_post_obj = 0, c_dpost = 0;
     __syncthreads();
 
+    const long long n_obj = (long long)P.ctr->n_heavy;
     for (;;) {
         if (tid == 0) s_obj = (long long)atomicAdd(&P.ctr->work, 1ull);
         __syncthreads();
-        const int64_t i = s_obj;
-        if (i >= P.N) break;
+        if (s_obj >= n_obj) break;
+        const int64_t i = P.heavy_ids[s_obj];
         int64_t rb = P.row_ptr[i], re = P.row_ptr[i + 1];
         if (P.checked && (rb < 0 || re < rb || re > P.nnz)) {
             // the borrowed CSR changed since it was validated: record it, read nothing
@@ -893,6 +897,277 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
     }
 }
 
+// ---------------- object lists and the warp-per-object (light) path ----------------
+//
+// Late in a run most objects are filtered (Algorithm 4, line 6: their own
+// cluster is invariant) and the moving clusters are few, so an object's scan
+// is short (its fronts) while the CTA-per-object kernel still pays a fixed
+// chain of global round trips and barriers per object. Such objects go to a
+// kernel where one warp scores one object with no block-wide barrier, its
+// scores in a per-warp slice of shared memory. The warp stages the object's
+// terms in the chunks the CTA kernel uses (P.chunk terms) and forms every
+// dense chain and every fixed-point add as that kernel does, so both compute
+// the same scores, labels and own scores.
+
+constexpr int LIGHT_WARPS = 8;      // warps per CTA of the light kernel
+constexpr int LIGHT_MAX = 1024;     // score slots per warp: the largest moving count of a light object
+
+__device__ __forceinline__ int instance_of(const AssignParams &P, int64_t i) {
+    int lo = 0, hi = P.n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.inst_obj[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Objects into the two lists: filtered objects of an instance with at most
+// light_max moving clusters to the light list, every other object to the
+// heavy list (warp-aggregated appends; the order inside a list changes no
+// result, every object is scored on its own).
+__global__ void k_classify(AssignParams P, int light_max, int32_t *heavy_ids, int32_t *light_ids) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < P.N; i0 += stride) {
+        const int64_t i = i0 + lane;
+        const bool valid = i < P.N;
+        bool light = false;
+        if (valid && light_max > 0) {
+            const int32_t a = P.labels_prev[i];
+            if (a >= 0 && P.own[i] != OWN_INVALID && P.lam_prev[a] != 0) {
+                const int m = instance_of(P, i);
+                light = P.mov_beg[m + 1] - P.mov_beg[m] <= light_max;
+            }
+        }
+        const unsigned ml = __ballot_sync(0xffffffffu, valid && light);
+        const unsigned mh = __ballot_sync(0xffffffffu, valid && !light);
+        unsigned bl = 0, bh = 0;
+        if (lane == 0) {
+            if (ml) bl = atomicAdd(&P.ctr->n_light, (unsigned)__popc(ml));
+            if (mh) bh = atomicAdd(&P.ctr->n_heavy, (unsigned)__popc(mh));
+        }
+        bl = __shfl_sync(0xffffffffu, bl, 0);
+        bh = __shfl_sync(0xffffffffu, bh, 0);
+        const unsigned below = (1u << lane) - 1u;
+        if (valid && light) light_ids[bl + __popc(ml & below)] = (int32_t)i;
+        if (valid && !light) heavy_ids[bh + __popc(mh & below)] = (int32_t)i;
+    }
+}
+
+template <int PREC, bool CID16>
+__global__ void __launch_bounds__(LIGHT_WARPS * 32, 4) assign_light_kernel(AssignParams P) {
+    __shared__ __align__(16) uint32_t s_rho[LIGHT_WARPS][LIGHT_MAX];
+    __shared__ int2 s_dn[LIGHT_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned FULL = 0xffffffffu, below = (1u << lane) - 1u;
+    uint32_t *rho = s_rho[w];
+    int2 *dn = s_dn[w];
+    // counters kept by lane 0: filtered, sim-calcs, changed, re-scored, candidates, dense entries
+    unsigned long long c_filt = 0, c_sim = 0, c_chg = 0, c_resc = 0, c_cand = 0, c_dent = 0;
+    unsigned long long c_post = 0, c_dpost = 0;  // every lane
+    const long long n_obj = (long long)P.ctr->n_light;
+    for (;;) {
+        long long li = 0;
+        if (lane == 0) li = (long long)atomicAdd(&P.ctr->work_light, 1ull);
+        li = __shfl_sync(FULL, li, 0);
+        if (li >= n_obj) break;
+        const int64_t i = P.light_ids[li];
+        int64_t rb = P.row_ptr[i], re = P.row_ptr[i + 1];
+        if (P.checked && (rb < 0 || re < rb || re > P.nnz)) {
+            if (lane == 0) atomicOr(&P.ctr->error, 1ull);
+            rb = re = 0;
+        }
+        const int inst = instance_of(P, i);
+        const int k_off = P.inst_k[inst];
+        const int n_mov = P.mov_beg[inst + 1] - P.mov_beg[inst];
+        const int32_t a_prev = P.labels_prev[i];
+        const int a_loc = a_prev - k_off;
+        const uint32_t own_q = P.own[i];
+        if (lane == 0) {
+            ++c_filt;
+            c_sim += (unsigned long long)n_mov;
+        }
+        if (n_mov == 0) {  // the own cluster is the only candidate: label and own score stay
+            if (lane == 0) P.labels[i] = a_prev;
+            continue;
+        }
+        for (int p = lane; p < n_mov; p += 32) rho[p] = 0u;
+        __syncwarp();
+        int nd_obj = 0;
+        for (int64_t cb = rb; cb < re; cb += P.chunk) {
+            const int64_t ce = min(re, cb + (int64_t)P.chunk);
+            // dense rows: the front (positions below n_mov) of each dense term of the chunk
+            for (int base = 0; base < n_mov; base += 256) {
+                const int p = base + 8 * lane;
+                float acc[8];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) acc[m] = 0.f;
+                int nd_chunk = 0;
+                for (int64_t s0 = cb; s0 < ce; s0 += 32) {
+                    const int64_t h = s0 + lane;
+                    int2 e = make_int2(-1, 0);
+                    if (h < ce) {
+                        int t = P.idx[h];
+                        if (P.checked && (t < 0 || t >= P.D)) {
+                            atomicOr(&P.ctr->error, 2ull);
+                            t = -1;
+                        }
+                        const int dr = t >= 0 ? P.dense_row[t] : -1;
+                        if (dr >= 0) {
+                            float vs = P.val[h] * FIX_SCALE;
+                            if constexpr (PREC == SIVF_FP16) vs *= FP16_INV_SCALE;
+                            e = make_int2(dr, __float_as_int(vs));
+                        }
+                    }
+                    const unsigned m = __ballot_sync(FULL, e.x >= 0);
+                    if (e.x >= 0) dn[__popc(m & below)] = e;
+                    __syncwarp();
+                    const int cnt = __popc(m);
+                    if (p < n_mov)
+                        for (int d = 0; d < cnt; ++d) {  // staging (term) order
+                            const int2 x = dn[d];
+                            fma_raw8<PREC>(load_raw8<PREC>(P.dense, (int64_t)x.x * 8 + p), __int_as_float(x.y), acc);
+                        }
+                    nd_chunk += cnt;
+                    __syncwarp();
+                }
+                if (p < n_mov) {
+#pragma unroll
+                    for (int m = 0; m < 8; ++m)
+                        if (p + m < n_mov && acc[m] > 0.f) rho[p + m] += __float2uint_ru(acc[m]);
+                }
+                if (base == 0) {
+                    nd_obj += nd_chunk;
+                    if (lane == 0) c_dent += (unsigned long long)nd_chunk * (unsigned long long)n_mov;
+                }
+            }
+            __syncwarp();
+            // sparse fronts of the chunk's other terms, one segment at a time, lane-strided
+            for (int64_t s0 = cb; s0 < ce; s0 += 32) {
+                const int64_t h = s0 + lane;
+                int len = 0, sb = 0, fb = 0;
+                float vs = 0.f;
+                if (h < ce) {
+                    int t = P.idx[h];
+                    if (P.checked && (t < 0 || t >= P.D)) t = -1;
+                    if (t >= 0) {
+                        len = P.if_mf0[t];
+                        c_post += (unsigned long long)len;
+                        if (P.dense_row[t] >= 0) {
+                            c_dpost += (unsigned long long)len;
+                            len = 0;
+                        } else {
+                            sb = (int)P.sc_off[t];
+                            fb = (int)(P.if_off[t + 1] - P.if_off[t]) & ~(SC_BLK - 1);
+                            vs = P.val[h] * FIX_SCALE;
+                        }
+                    }
+                }
+                unsigned m = __ballot_sync(FULL, len > 0);
+                while (m) {
+                    const int src = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int L = __shfl_sync(FULL, len, src), b = __shfl_sync(FULL, sb, src);
+                    const int f = __shfl_sync(FULL, fb, src);
+                    const float v = __shfl_sync(FULL, vs, src);
+                    for (int o = lane; o < L; o += 32) {
+                        int id;
+                        float u;
+                        load_one<PREC, CID16>(P, b + tiled_offset(o, f), id, u);
+                        atomicAdd(rho + id, __float2uint_ru(v * u));
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        // argmax over the moving clusters plus the own cluster (carried score)
+        Top2 t;
+        t.bv = 0u;
+        t.bi = INT32_MAX;
+        t.sv = -1;
+        for (int p = lane; p < n_mov; p += 32) {
+            const uint32_t v = rho[p];
+            if (t.bi == INT32_MAX || v >= t.bv) top2_push(t, v, P.pos_clu[k_off + p]);
+            else t.sv = max(t.sv, (long long)v);
+        }
+        if (lane == 0) top2_push(t, own_q, a_loc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t = top2_merge(t, top2_shfl(t, o));
+        int winner = t.bi;
+        if (t.bv > 0u && t.sv >= 0) {
+            // the carried own score may come from a scan with other dense terms:
+            // count every term as dense
+            const double best = (double)t.bv * FIX_QUANTUM;
+            const double E = error_bound(best, re - rb, (int)(re - rb), (double)P.sumv[i], P.eps, P.eta);
+            const double gap = (double)((long long)t.bv - t.sv) * FIX_QUANTUM;
+            if (gap <= 2.0 * E) {
+                const double span = ceil(2.0 * E / FIX_QUANTUM);
+                const uint32_t thr = span >= (double)t.bv ? 0u : t.bv - (uint32_t)span;
+                double wbest = -1.0;
+                int wj = INT32_MAX, ncand = 0;
+                for (int base = 0; base < n_mov; base += 32) {
+                    const int p = base + lane;
+                    const int j = (p < n_mov && rho[p] >= thr) ? P.pos_clu[k_off + p] : -1;
+                    unsigned bal = __ballot_sync(FULL, j >= 0);
+                    while (bal) {
+                        const int src = __ffs(bal) - 1;
+                        bal &= bal - 1;
+                        const int jc = __shfl_sync(FULL, j, src);
+                        const double x = exact_score(P, rb, re, k_off + jc, lane);
+                        ++ncand;
+                        if (x > wbest || (x == wbest && jc < wj)) {
+                            wbest = x;
+                            wj = jc;
+                        }
+                    }
+                }
+                if (own_q >= thr) {
+                    const double x = exact_score(P, rb, re, a_prev, lane);
+                    ++ncand;
+                    if (x > wbest || (x == wbest && a_loc < wj)) {
+                        wbest = x;
+                        wj = a_loc;
+                    }
+                }
+                if (wj != INT32_MAX) winner = wj;
+                if (lane == 0) {
+                    ++c_resc;
+                    c_cand += (unsigned long long)ncand;
+                }
+            }
+        }
+        if (lane == 0) {
+            const int a = k_off + winner;
+            P.labels[i] = a;
+            P.own[i] = winner == a_loc ? own_q : rho[P.clu_pos[a]];
+            if (a != a_prev) {
+                ++c_chg;
+                P.moving[a] = 1;
+                P.moving[a_prev] = 1;
+                if (P.n_inst > 1) atomicAdd(P.inst_changed + inst, 1ull);
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c_post += __shfl_xor_sync(FULL, c_post, o);
+        c_dpost += __shfl_xor_sync(FULL, c_dpost, o);
+    }
+    if (lane == 0) {
+        if (c_post) atomicAdd(&P.ctr->postings, c_post);
+        if (c_dpost) atomicAdd(&P.ctr->dense_postings, c_dpost);
+        if (c_filt) atomicAdd(&P.ctr->filtered, c_filt);
+        if (c_sim) atomicAdd(&P.ctr->simcalc, c_sim);
+        if (c_chg) atomicAdd(&P.ctr->changed, c_chg);
+        if (c_resc) {
+            atomicAdd(&P.ctr->rescored, c_resc);
+            atomicAdd(&P.ctr->rescore_cands, c_cand);
+        }
+        if (c_dent) atomicAdd(&P.ctr->dense_entries, c_dent);
+    }
+}
+
 // lambda^[r] from the moving flags, the ascending list of moving ids, and
 // where each instance's moving ids start in that list.
 __global__ void __launch_bounds__(1024) finalize_kernel(int32_t k, int first_iter, const uint8_t *moving,
@@ -1028,6 +1303,34 @@ cudaError_t launch_assign(sivf_ctx *c) {
     } else {
         P.eps = 0.0;
         P.eta = 0.0;
+    }
+    P.heavy_ids = c->heavy_ids;
+    P.light_ids = c->light_ids;
+    P.chunk = c->assign_threads;
+    // objects into the light and heavy lists, the light ones scored first
+    const int light_max = (c->cfg.icp == 1 || c->cfg.icp == 3) ? LIGHT_MAX : 0;
+    k_classify<<<(unsigned)std::min<int64_t>((c->N + 255) / 256, (int64_t)c->num_sms * 8), 256, 0, c->stream>>>(
+        P, light_max, c->heavy_ids, c->light_ids);
+    note_launch();
+    SIVF_CUDA_TRY(cudaGetLastError());
+    if (light_max > 0) {
+        const bool ids16 = P.sc_id16 || P.sc_pack;
+        const unsigned grid = (unsigned)c->num_sms * 4;
+        switch (c->cfg.prec) {
+            case SIVF_BF16:
+                if (ids16) assign_light_kernel<SIVF_BF16, true><<<grid, LIGHT_WARPS * 32, 0, c->stream>>>(P);
+                else assign_light_kernel<SIVF_BF16, false><<<grid, LIGHT_WARPS * 32, 0, c->stream>>>(P);
+                break;
+            case SIVF_FP16:
+                if (ids16) assign_light_kernel<SIVF_FP16, true><<<grid, LIGHT_WARPS * 32, 0, c->stream>>>(P);
+                else assign_light_kernel<SIVF_FP16, false><<<grid, LIGHT_WARPS * 32, 0, c->stream>>>(P);
+                break;
+            default:
+                if (ids16) assign_light_kernel<SIVF_FP32, true><<<grid, LIGHT_WARPS * 32, 0, c->stream>>>(P);
+                else assign_light_kernel<SIVF_FP32, false><<<grid, LIGHT_WARPS * 32, 0, c->stream>>>(P);
+        }
+        note_launch();
+        SIVF_CUDA_TRY(cudaGetLastError());
     }
     switch (c->cfg.prec) {
         case SIVF_BF16: return launch_ids<SIVF_BF16>(c, P);

@@ -90,7 +90,8 @@ struct DevCounters {
     unsigned long long dense_postings;  // postings of the scanned segments held in dense rows
     long long dense_terms;              // terms with a dense row (last inverted-file build)
     long long dense_used;               // dense-row entries in use / 8 (last build)
-    unsigned long long pad[1];
+    unsigned long long work_light;   // object work counter of the light (warp-per-object) kernel
+    unsigned int n_heavy, n_light;   // objects in the two lists of the assignment
 };
 
 // Bump allocator over one device block (scratch that lives for one step).
@@ -200,6 +201,10 @@ struct sivf_ctx {
     uint32_t *grho = nullptr; // global score vectors: grho_ctas slabs of kmax (zero between objects)
     int64_t grho_ctas = 0;
     unsigned long long launch_base = 0;  // g_launches at init / reseed
+    // object lists of the assignment: filtered objects of instances with few
+    // moving clusters take the warp-per-object kernel (light), the rest the
+    // CTA-per-object kernel (heavy)
+    int32_t *heavy_ids = nullptr, *light_ids = nullptr;
 
     // independent instances sharing one context: objects [inst_obj[m],
     // inst_obj[m+1]), clusters [inst_k[m], inst_k[m+1]), terms [inst_d[m],
