@@ -75,6 +75,10 @@ def parse():
                     help="device memory for dense head-term rows (0 = automatic, < 0 = none)")
     ap.add_argument("--dense-min-fraction", type=float, default=0.0,
                     help="list length / k from which a term gets a dense row (0 = automatic)")
+    ap.add_argument("--dense-all", action="store_true",
+                    help="every term from a dense row: the dense-mean variant (Lloyd-ICP with dense means)")
+    ap.add_argument("--light-max-moving", type=int, default=0,
+                    help="warp-per-object path up to this many moving clusters (0 = automatic, < 0 = off)")
     ap.add_argument("--update-mode", default="auto", choices=["auto", "dense", "sort"],
                     help="cluster sums of the update step (sort: no k x D accumulator, for small captures)")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 comparison path")
@@ -380,7 +384,8 @@ class Path:
         self.g = SIVF(rp, ix, vl, c.D, w.k, ini, precision=precision, icp=args.icp, threads=args.threads,
                       ctas_per_sm=args.ctas_per_sm, autotune=bool(args.autotune),
                       dense_max_bytes=int(args.dense_max_mb * 2**20) if args.dense_max_mb >= 0 else -1,
-                      dense_min_fraction=args.dense_min_fraction, update_mode=args.update_mode)
+                      dense_min_fraction=args.dense_min_fraction, update_mode=args.update_mode,
+                      dense_all=args.dense_all, light_max_moving=args.light_max_moving)
         self.converged = False
         self.resets = 0
 
@@ -667,6 +672,7 @@ def main():
                               "filtered": [int(p["filtered"]) for p in per],
                               "rescored": [int(p["rescored"]) for p in per],
                               "changed": [int(p["changed"]) for p in per],
+                              "n_moving_prev": [int(p["n_moving_prev"]) for p in per],
                               "ms_assign": [round(p["ms_assign"], 3) for p in per],
                               "ms_update": [round(p["ms_update"], 3) for p in per]},
             "gpu_launches": int(launches) if launches is not None else None,

@@ -118,6 +118,18 @@ typedef struct {
                             fraction of its instance's k (the threshold rises while the
                             rows would exceed dense_max_bytes); 0 = automatic (0.25).
                             Must be in [0, 1]. IVF-CBICP (icp = 2) uses no dense rows */
+    int light_max_moving;     /* filtered objects (own cluster invariant) of an instance with
+                            at most this many moving clusters are scored by one warp each
+                            instead of one CTA each (same scores, labels and counts; no
+                            block-wide barrier per object). 0 = automatic (1472, the
+                            largest allowed), < 0 = every object in the CTA kernel. Used
+                            with icp = 1 and 3 */
+    int dense_all;            /* 1: every term gets a dense row, whatever its length: the
+                            centroids are held as a dense matrix (k x 2 or k x 4 bytes per
+                            term, in scan order), the dense-mean variant of the scan
+                            (Lloyd-ICP with full-expression means, as the paper's
+                            comparison systems keep them; Section 3). Same labels;
+                            dense_max_bytes and dense_min_fraction are then ignored */
 } sivf_config;
 
 /* Counters of the most recent assignment / update (host copy). */
@@ -153,6 +165,8 @@ typedef struct {
                                 rest were read one posting at a time) */
     int64_t dense_terms;     /* terms with a dense row in the current inverted file */
     int64_t dense_row_entries; /* entries of those rows (padded to multiples of 8) */
+    int64_t light_objects;   /* objects of the last assignment scored one warp each (filtered
+                                objects of instances with few moving clusters) */
 } sivf_stats;
 
 typedef struct sivf_ctx sivf_ctx; /* opaque, library-owned */

@@ -78,6 +78,7 @@ cudaError_t read_file_counters(sivf_ctx *c) {
     SIVF_CUDA_TRY(cudaStreamSynchronize(c->stream));
     c->dense_terms_h = c->ctr_host->dense_terms;
     c->dense_used_h = c->ctr_host->dense_used * 8;
+    c->sparse_entries_h = c->ctr_host->sparse_entries;
     return cudaSuccess;
 }
 
@@ -251,7 +252,18 @@ sivf_status create_ctx(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_
         const int64_t esize = c->cfg.prec == SIVF_FP32 ? 4 : 2;
         const int64_t bytes = c->cfg.dense_max_bytes == 0 ? (int64_t)96 << 20 : c->cfg.dense_max_bytes;
         c->cap_dense = (c->cfg.icp == 2 || bytes < 0) ? 0 : (bytes / esize) & ~(int64_t)7;
+        if (c->cfg.dense_all && c->cfg.icp != 2) {  // room for a row of every term
+            c->cap_dense = 0;
+            for (int32_t m = 0; m < ni; ++m)
+                c->cap_dense += (int64_t)(inst_d[(size_t)m + 1] - inst_d[(size_t)m]) *
+                                ((inst_k[(size_t)m + 1] - inst_k[(size_t)m] + 7) & ~7);
+        }
         c->dense_frac = c->cfg.dense_min_fraction > 0.f ? c->cfg.dense_min_fraction : 0.25f;
+        if (c->cap_dense / 8 >= 0x7FFFFFFFll) {  // rows are addressed in 8-entry units with 32 bits
+            free_all(c);
+            delete c;
+            return SIVF_ERR_INVALID_ARG;
+        }
         if (c->cap_dense > 0) INIT_CUDA(dmalloc(c, reinterpret_cast<uint16_t **>(&c->dense_val),
                                                 (size_t)(c->cap_dense * esize / 2)), "alloc dense rows");
     }
@@ -411,7 +423,8 @@ sivf_status sivf_init(sivf_ctx **out, const sivf_config *cfg, int64_t N, int32_t
         !init_ids)
         return SIVF_ERR_INVALID_ARG;
     if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16 || cfg->icp < 0 || cfg->icp > 3 ||
-                !(cfg->dense_min_fraction >= 0.f && cfg->dense_min_fraction <= 1.f)))
+                !(cfg->dense_min_fraction >= 0.f && cfg->dense_min_fraction <= 1.f) ||
+                cfg->light_max_moving > 1472))
         return SIVF_ERR_INVALID_ARG;
     if (!distinct_ids(init_ids, k, N)) return SIVF_ERR_INVALID_ARG;
     if (cfg && cfg->inputs_on_host) {
@@ -455,7 +468,8 @@ sivf_status sivf_batch_init(sivf_ctx **out, const sivf_config *cfg, int32_t n_in
     *out = nullptr;
     if (n_inst < 1 || n_inst > 65536 || !descs) return SIVF_ERR_INVALID_ARG;
     if (cfg && (cfg->prec < SIVF_FP32 || cfg->prec > SIVF_FP16 || cfg->inputs_on_host || cfg->icp < 0 || cfg->icp > 3 ||
-                !(cfg->dense_min_fraction >= 0.f && cfg->dense_min_fraction <= 1.f)))
+                !(cfg->dense_min_fraction >= 0.f && cfg->dense_min_fraction <= 1.f) ||
+                cfg->light_max_moving > 1472))
         return SIVF_ERR_INVALID_ARG;
     std::vector<int64_t> inst_obj(1, 0);
     std::vector<int32_t> inst_k(1, 0), inst_d(1, 0);
@@ -637,6 +651,7 @@ sivf_status finish_assign(sivf_ctx *c, int64_t *n_changed, float ms) {
     st.rescore_cands = (int64_t)h.rescore_cands;
     st.dense_entries = (int64_t)h.dense_entries;
     st.dense_postings = (int64_t)h.dense_postings;
+    st.light_objects = (int64_t)h.n_light;
     if (ms >= 0.f) st.ms_assign = ms;
     if (n_changed) *n_changed = st.changed;
     return SIVF_OK;
@@ -652,6 +667,7 @@ sivf_status finish_update(sivf_ctx *c, float ms) {
     c->if_nnz = c->c_nnz;
     c->dense_terms_h = c->ctr_host->dense_terms;
     c->dense_used_h = c->ctr_host->dense_used * 8;
+    c->sparse_entries_h = c->ctr_host->sparse_entries;
     c->stats.moved_nnz = c->ctr_host->moved;
     double ja = 0.0, ju = 0.0;
     for (int32_t m = 0; m < c->n_inst; ++m) {

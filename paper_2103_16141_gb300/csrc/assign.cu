@@ -71,6 +71,7 @@ struct AssignParams {
     const int32_t *heavy_ids;  // objects of the CTA-per-object kernel (ctr->n_heavy of them)
     const int32_t *light_ids;  // objects of the warp-per-object kernel (ctr->n_light of them)
     int chunk;                 // terms staged per chunk by the CTA kernel (its block size)
+    int stream_sparse;         // 1: the sparse scan copy exceeds L2; its loads are streamed
     uint32_t *grho;            // global score vectors, one kmax slab per CTA (global score-buffer variant)
     const int64_t *coff;
     const int32_t *cterm;
@@ -252,6 +253,37 @@ __device__ __forceinline__ int tiled_offset(int o, int fb) {
 
 constexpr int CH = 2 * SC_BLK;  // postings per fast item: two blocks of the tiled layout
 
+// L2 eviction priority (createpolicy + ld.global.nc.L2::cache_hint): when the
+// sparse posting lists do not fit in L2 they are streamed (evict_first), so
+// that they do not push the dense rows, read by every object, out of it.
+// Measured on the 8M x 140K, k = 20,000 corpus: 5 % (BF16) and 6 % (FP32)
+// shorter assignments; marking the dense rows evict_last as well changed
+// nothing. On a corpus whose sparse copy fits in L2 the hint is not used.
+__device__ __forceinline__ uint64_t pol_stream() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint4 ld_hint_v4(const void *ptr, uint64_t pol) {
+    uint4 r;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(ptr), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint2 ld_hint_v2(const void *ptr, uint64_t pol) {
+    uint2 r;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(r.x), "=r"(r.y) : "l"(ptr), "l"(pol));
+    return r;
+}
+// 16 bytes of the sparse scan copy: streamed when the copy exceeds L2
+__device__ __forceinline__ uint4 ld_sparse_v4(const void *ptr, bool stream) {
+    return stream ? ld_hint_v4(ptr, pol_stream()) : __ldg(static_cast<const uint4 *>(ptr));
+}
+__device__ __forceinline__ uint2 ld_sparse_v2(const void *ptr, bool stream) {
+    return stream ? ld_hint_v2(ptr, pol_stream()) : __ldg(static_cast<const uint2 *>(ptr));
+}
+
 template <int PREC>
 __device__ __forceinline__ float decode_u(unsigned b) {
     if constexpr (PREC == SIVF_BF16) return __uint_as_float(b << 16);
@@ -271,7 +303,7 @@ template <int PREC, bool CID16>
 __device__ __forceinline__ Post4 load_tiled(const AssignParams &P, int pos) {
     Post4 r;
     if constexpr (CID16 && PREC != SIVF_FP32) {
-        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(P.sc_pack + pos));
+        const uint4 w = ld_sparse_v4(P.sc_pack + pos, P.stream_sparse);
         const unsigned ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
@@ -281,26 +313,28 @@ __device__ __forceinline__ Post4 load_tiled(const AssignParams &P, int pos) {
         return r;
     } else {
         if constexpr (CID16) {
-            const uint2 w = __ldg(reinterpret_cast<const uint2 *>(P.sc_id16 + pos));
+            const uint2 w = ld_sparse_v2(P.sc_id16 + pos, P.stream_sparse);
             r.id[0] = (int)(w.x & 0xFFFFu);
             r.id[1] = (int)(w.x >> 16);
             r.id[2] = (int)(w.y & 0xFFFFu);
             r.id[3] = (int)(w.y >> 16);
         } else {
-            const int4 w = __ldg(reinterpret_cast<const int4 *>(P.sc_id32 + pos));
-            r.id[0] = w.x;
-            r.id[1] = w.y;
-            r.id[2] = w.z;
-            r.id[3] = w.w;
+            const uint4 w = ld_sparse_v4(P.sc_id32 + pos, P.stream_sparse);
+            r.id[0] = (int)w.x;
+            r.id[1] = (int)w.y;
+            r.id[2] = (int)w.z;
+            r.id[3] = (int)w.w;
         }
         if constexpr (PREC == SIVF_FP32) {
-            const float4 v = __ldg(reinterpret_cast<const float4 *>(P.sc_val + pos));
+            const uint4 vw = ld_sparse_v4(P.sc_val + pos, P.stream_sparse);
+            const float4 v = make_float4(__uint_as_float(vw.x), __uint_as_float(vw.y), __uint_as_float(vw.z),
+                                         __uint_as_float(vw.w));
             r.u[0] = v.x;
             r.u[1] = v.y;
             r.u[2] = v.z;
             r.u[3] = v.w;
         } else {
-            const uint2 v = __ldg(reinterpret_cast<const uint2 *>(P.sc_lp + pos));
+            const uint2 v = ld_sparse_v2(P.sc_lp + pos, P.stream_sparse);
             r.u[0] = decode_u<PREC>(v.x & 0xFFFFu);
             r.u[1] = decode_u<PREC>(v.x >> 16);
             r.u[2] = decode_u<PREC>(v.y & 0xFFFFu);
@@ -909,8 +943,14 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
 // dense chain and every fixed-point add as that kernel does, so both compute
 // the same scores, labels and own scores.
 
-constexpr int LIGHT_WARPS = 8;      // warps per CTA of the light kernel
-constexpr int LIGHT_MAX = 1024;     // score slots per warp: the largest moving count of a light object
+// 8 warps per CTA, 1,472 score slots each (the moving clusters' scores), so
+// that a CTA's static shared memory is 48 KB; 4 CTAs per SM. On the
+// 8M x 140K, k = 20,000 corpus one warp per object beat one CTA per object
+// up to about 1,500 moving clusters (1,156: 553 vs 623 ms, 1,284: 623 vs
+// 648 ms per assignment) and lost above (1,802: 800 vs 726 ms).
+constexpr int LIGHT_WARPS = 8;
+constexpr int LIGHT_MAX = 1472;  // the largest moving count of a light object
+static_assert(LIGHT_WARPS * (LIGHT_MAX * 4 + 32 * 8) <= 48 * 1024, "static shared memory of the light kernel");
 
 __device__ __forceinline__ int instance_of(const AssignParams &P, int64_t i) {
     int lo = 0, hi = P.n_inst - 1;
@@ -949,8 +989,9 @@ __global__ void k_classify(AssignParams P, int light_max, int32_t *heavy_ids, in
         bl = __shfl_sync(0xffffffffu, bl, 0);
         bh = __shfl_sync(0xffffffffu, bh, 0);
         const unsigned below = (1u << lane) - 1u;
-        if (valid && light) light_ids[bl + __popc(ml & below)] = (int32_t)i;
-        if (valid && !light) heavy_ids[bh + __popc(mh & below)] = (int32_t)i;
+        if (!valid) continue;
+        if (light) light_ids[bl + __popc(ml & below)] = (int32_t)i;
+        else heavy_ids[bh + __popc(mh & below)] = (int32_t)i;
     }
 }
 
@@ -1251,6 +1292,16 @@ cudaError_t launch_ids(sivf_ctx *c, const AssignParams &P) {
     return ids16 ? launch_prec<PREC, true, false>(c, P) : launch_prec<PREC, false, false>(c, P);
 }
 
+template <int PREC>
+cudaError_t launch_light(sivf_ctx *c, const AssignParams &P) {
+    const bool ids16 = P.sc_id16 || P.sc_pack;
+    const unsigned grid = (unsigned)c->num_sms * 4;  // one wave of resident CTAs
+    if (ids16) assign_light_kernel<PREC, true><<<grid, LIGHT_WARPS * 32, 0, c->stream>>>(P);
+    else assign_light_kernel<PREC, false><<<grid, LIGHT_WARPS * 32, 0, c->stream>>>(P);
+    note_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_assign(sivf_ctx *c) {
@@ -1307,30 +1358,25 @@ cudaError_t launch_assign(sivf_ctx *c) {
     P.heavy_ids = c->heavy_ids;
     P.light_ids = c->light_ids;
     P.chunk = c->assign_threads;
+    {
+        const int64_t b_post = c->cfg.prec == SIVF_FP32 ? 6 : 4;
+        P.stream_sparse = c->sparse_entries_h * b_post > (int64_t)64 << 20 ? 1 : 0;  // half of the L2
+    }
     // objects into the light and heavy lists, the light ones scored first
-    const int light_max = (c->cfg.icp == 1 || c->cfg.icp == 3) ? LIGHT_MAX : 0;
+    const int cap = c->cfg.light_max_moving;
+    const int light_max = (c->cfg.icp == 1 || c->cfg.icp == 3) && cap >= 0 ? (cap == 0 ? LIGHT_MAX : cap) : 0;
     k_classify<<<(unsigned)std::min<int64_t>((c->N + 255) / 256, (int64_t)c->num_sms * 8), 256, 0, c->stream>>>(
         P, light_max, c->heavy_ids, c->light_ids);
     note_launch();
     SIVF_CUDA_TRY(cudaGetLastError());
     if (light_max > 0) {
-        const bool ids16 = P.sc_id16 || P.sc_pack;
-        const unsigned grid = (unsigned)c->num_sms * 4;
+        cudaError_t e;
         switch (c->cfg.prec) {
-            case SIVF_BF16:
-                if (ids16) assign_light_kernel<SIVF_BF16, true><<<grid, LIGHT_WARPS * 32, 0, c->stream>>>(P);
-                else assign_light_kernel<SIVF_BF16, false><<<grid, LIGHT_WARPS * 32, 0, c->stream>>>(P);
-                break;
-            case SIVF_FP16:
-                if (ids16) assign_light_kernel<SIVF_FP16, true><<<grid, LIGHT_WARPS * 32, 0, c->stream>>>(P);
-                else assign_light_kernel<SIVF_FP16, false><<<grid, LIGHT_WARPS * 32, 0, c->stream>>>(P);
-                break;
-            default:
-                if (ids16) assign_light_kernel<SIVF_FP32, true><<<grid, LIGHT_WARPS * 32, 0, c->stream>>>(P);
-                else assign_light_kernel<SIVF_FP32, false><<<grid, LIGHT_WARPS * 32, 0, c->stream>>>(P);
+            case SIVF_BF16: e = launch_light<SIVF_BF16>(c, P); break;
+            case SIVF_FP16: e = launch_light<SIVF_FP16>(c, P); break;
+            default: e = launch_light<SIVF_FP32>(c, P);
         }
-        note_launch();
-        SIVF_CUDA_TRY(cudaGetLastError());
+        SIVF_CUDA_TRY(e);
     }
     switch (c->cfg.prec) {
         case SIVF_BF16: return launch_ids<SIVF_BF16>(c, P);

@@ -92,6 +92,7 @@ struct DevCounters {
     long long dense_used;               // dense-row entries in use / 8 (last build)
     unsigned long long work_light;   // object work counter of the light (warp-per-object) kernel
     unsigned int n_heavy, n_light;   // objects in the two lists of the assignment
+    long long sparse_entries;        // entries of the sparse scan copy (last build)
 };
 
 // Bump allocator over one device block (scratch that lives for one step).
@@ -205,6 +206,7 @@ struct sivf_ctx {
     // moving clusters take the warp-per-object kernel (light), the rest the
     // CTA-per-object kernel (heavy)
     int32_t *heavy_ids = nullptr, *light_ids = nullptr;
+    long long sparse_entries_h = 0;  // entries of the sparse scan copy (host copy, for the L2 hint)
 
     // independent instances sharing one context: objects [inst_obj[m],
     // inst_obj[m+1]), clusters [inst_k[m], inst_k[m+1]), terms [inst_d[m],

@@ -21,6 +21,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "sivf_internal.cuh"
 
 namespace sivf {
@@ -737,12 +739,13 @@ __device__ __forceinline__ void term_bin(int32_t t, int32_t n_inst, const int32_
     *bin = (int)(q < DENSE_BINS ? q : DENSE_BINS);
 }
 
-// Histogram of the dense-row entries each length bin would take.
+// Histogram of the dense-row entries each length bin would take (lists of at
+// least min_len postings).
 __global__ void k_dense_hist(int32_t D, int32_t n_inst, const int32_t *inst_d, const int32_t *inst_k,
-                             const int64_t *len, unsigned long long *hist) {
+                             const int64_t *len, int64_t min_len, unsigned long long *hist) {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < D; g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t L = len[g];
-        if (L < DENSE_MIN_LEN) continue;
+        if (L < min_len) continue;
         int32_t km;
         int bin;
         term_bin((int32_t)g, n_inst, inst_d, inst_k, L, &km, &bin);
@@ -767,12 +770,12 @@ __global__ void k_dense_threshold(const unsigned long long *hist, int bmin, unsi
 // Dense-row width (in 8-entry units) of every term; the sparse scan copy
 // gives dense terms no room.
 __global__ void k_dense_width(int32_t D, int32_t n_inst, const int32_t *inst_d, const int32_t *inst_k,
-                              const int64_t *len, const int32_t *thr, int64_t *w8, int64_t *slen) {
+                              const int64_t *len, int64_t min_len, const int32_t *thr, int64_t *w8, int64_t *slen) {
     const int b = *thr;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < D; g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t L = len[g];
         int64_t w = 0;
-        if (L >= DENSE_MIN_LEN) {
+        if (L >= min_len) {
             int32_t km;
             int bin;
             term_bin((int32_t)g, n_inst, inst_d, inst_k, L, &km, &bin);
@@ -975,20 +978,23 @@ cudaError_t build_inverted_file(sivf_ctx *c) {
                                                  cb ? 1 : 0, c->clu_pos, c->pos_clu);
     note_launch(3);
     // dense head rows: the longest lists (relative to their instance's k) that
-    // fit in the row capacity, from dense_frac of k up
+    // fit in the row capacity, from dense_frac of k up; with dense_all every
+    // list (the dense-mean variant: all of the centroids as dense rows)
     SIVF_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (DENSE_BINS + 1), s));
-    const int bmin = (int)ceilf(c->dense_frac * DENSE_BINS);
+    const bool all = c->cfg.dense_all != 0;
+    const int bmin = all ? 0 : std::max(1, (int)ceilf(c->dense_frac * DENSE_BINS));
+    const int64_t min_len = all ? 1 : DENSE_MIN_LEN;
     const bool dense = c->cap_dense > 0 && !cb && bmin <= DENSE_BINS;
     if (dense) {
-        k_dense_hist<<<blocks_gs(D), TPB, 0, s>>>(D, c->n_inst, c->inst_d, c->inst_k, len, hist);
-        k_dense_threshold<<<1, 32, 0, s>>>(hist, bmin < 1 ? 1 : bmin, (unsigned long long)c->cap_dense,
-                                          c->dense_thr);
+        k_dense_hist<<<blocks_gs(D), TPB, 0, s>>>(D, c->n_inst, c->inst_d, c->inst_k, len, min_len, hist);
+        k_dense_threshold<<<1, 32, 0, s>>>(hist, bmin, (unsigned long long)c->cap_dense, c->dense_thr);
         note_launch(2);
     } else {  // no bin qualifies: the threshold becomes DENSE_BINS + 1 (no rows)
         k_dense_threshold<<<1, 32, 0, s>>>(hist, DENSE_BINS + 1, 0ull, c->dense_thr);
         note_launch();
     }
-    k_dense_width<<<blocks_gs(D), TPB, 0, s>>>(D, c->n_inst, c->inst_d, c->inst_k, len, c->dense_thr, w8, slen);
+    k_dense_width<<<blocks_gs(D), TPB, 0, s>>>(D, c->n_inst, c->inst_d, c->inst_k, len, min_len, c->dense_thr, w8,
+                                                slen);
     note_launch();
     SIVF_CUDA_TRY(cudaGetLastError());
     SIVF_CUDA_TRY(scan_exclusive_i64(len, c->if_off, D, total, ws, s));
@@ -1013,6 +1019,7 @@ cudaError_t build_inverted_file(sivf_ctx *c) {
                                                 c->sc_pack, c->sc_lp);
     note_launch();
     SIVF_CUDA_TRY(cudaMemcpyAsync(&c->ctr->dense_used, total + 2, sizeof(long long), cudaMemcpyDeviceToDevice, s));
+    SIVF_CUDA_TRY(cudaMemcpyAsync(&c->ctr->sparse_entries, total + 1, sizeof(long long), cudaMemcpyDeviceToDevice, s));
     SIVF_CUDA_TRY(cudaGetLastError());
     ws.used = mark;
     return cudaSuccess;

@@ -36,7 +36,8 @@ class sivf_config(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int), ("mem_cap_bytes", ctypes.c_int64), ("use_graph", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("score_buffer", ctypes.c_int), ("update_mode", ctypes.c_int),
                 ("inputs_on_host", ctypes.c_int), ("checked", ctypes.c_int),
-                ("dense_max_bytes", ctypes.c_int64), ("dense_min_fraction", ctypes.c_float)]
+                ("dense_max_bytes", ctypes.c_int64), ("dense_min_fraction", ctypes.c_float),
+                ("light_max_moving", ctypes.c_int), ("dense_all", ctypes.c_int)]
 
 
 class sivf_stats(ctypes.Structure):
@@ -49,7 +50,8 @@ class sivf_stats(ctypes.Structure):
                 ("graph_iters", ctypes.c_int64), ("assign_threads", ctypes.c_int32),
                 ("assign_global", ctypes.c_int32), ("update_dense", ctypes.c_int32),
                 ("dense_entries", ctypes.c_int64), ("dense_postings", ctypes.c_int64),
-                ("dense_terms", ctypes.c_int64), ("dense_row_entries", ctypes.c_int64)]
+                ("dense_terms", ctypes.c_int64), ("dense_row_entries", ctypes.c_int64),
+                ("light_objects", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -244,7 +246,7 @@ class SIVF:
                  threads: int = 0, ctas_per_sm: int = 0, mem_cap_bytes: int = 0, stream=None, use_graph: bool = False,
                  autotune: bool = False, score_buffer: str = "auto", inputs_on_host: bool = False,
                  update_mode: str = "auto", checked: bool = False, dense_max_bytes: int = 0,
-                 dense_min_fraction: float = 0.0):
+                 dense_min_fraction: float = 0.0, light_max_moving: int = 0, dense_all: bool = False):
         import numpy as np
         import torch
 
@@ -287,7 +289,8 @@ class SIVF:
         cfg = sivf_config(PRECISIONS[precision], icp_mode(icp), int(threads), int(ctas_per_sm), int(mem_cap_bytes),
                           int(bool(use_graph)), int(bool(autotune)), SCORE_BUFFERS[score_buffer],
                           UPDATE_MODES[update_mode], int(bool(inputs_on_host)), int(bool(checked)),
-                          int(dense_max_bytes), float(dense_min_fraction))
+                          int(dense_max_bytes), float(dense_min_fraction), int(light_max_moving),
+                          int(bool(dense_all)))
         self.ctx = sivf_init(cfg, self.N, self.D, self.k, rp_p, ix_p, vl_p, ini.ctypes.data, self.stream.cuda_stream)
 
     def close(self):
@@ -419,7 +422,8 @@ class SIVFBatch:
 
     def __init__(self, corpora, ks, init_ids, precision: str = "fp32", icp=True, threads: int = 0,
                  ctas_per_sm: int = 0, use_graph: bool = False, autotune: bool = False, score_buffer: str = "auto",
-                 update_mode: str = "auto", dense_max_bytes: int = 0, dense_min_fraction: float = 0.0):
+                 update_mode: str = "auto", dense_max_bytes: int = 0, dense_min_fraction: float = 0.0,
+                 light_max_moving: int = 0):
         import numpy as np
         import torch
 
@@ -445,7 +449,8 @@ class SIVFBatch:
         self.ks = [int(k) for k in ks]
         cfg = sivf_config(PRECISIONS[precision], icp_mode(icp), int(threads), int(ctas_per_sm), 0,
                           int(bool(use_graph)), int(bool(autotune)), SCORE_BUFFERS[score_buffer],
-                          UPDATE_MODES[update_mode], 0, 0, int(dense_max_bytes), float(dense_min_fraction))
+                          UPDATE_MODES[update_mode], 0, 0, int(dense_max_bytes), float(dense_min_fraction),
+                          int(light_max_moving))
         self.ctx = sivf_batch_init(cfg, descs)
         self._keep = None  # the library copied the corpora
 

@@ -112,3 +112,26 @@ def test_dense_rows_in_a_batch():
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_dense_mean_variant_equals_the_hybrid(precision):
+    """dense_all: every term is read from a dense row (the centroids as a
+    dense matrix in scan order, Lloyd-ICP with full-expression means). Same
+    labels, method-level counts and centroids as the default layout."""
+    w = CONFIGS["c2"].scaled(N=6_000, D=6_000, k=70)
+    c, ini = corpus_for(w, seed=73)
+    a = _run(c, w.k, ini, 12, precision=precision, dense_all=True)
+    b = _run(c, w.k, ini, 12, precision=precision)
+    st = a[3]
+    assert st["dense_postings"] == st["postings"], "every posting from a dense row"
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    for x, y in zip(a[2], b[2]):
+        assert np.array_equal(x, y)
+
+
+def test_dense_mean_variant_lockstep_with_the_oracle():
+    w = CONFIGS["c2"].scaled(N=4_000, D=5_000, k=60)
+    c, ini = corpus_for(w, seed=79)
+    recs = lockstep(c, w.k, ini, 8, dense_all=True)
+    assert all(r["stats"]["dense_postings"] == r["stats"]["postings"] for r in recs)
