@@ -501,8 +501,29 @@ __device__ __forceinline__ long long block_sum_ll(long long x, long long *sh) {
     return r;
 }
 
-// Pass 1, one CTA per cluster: size of the new row, ||s_j|| in FP64 (strided
-// per-thread sums, fixed tree) and <s_j, mu_j^[r-1]> over the previous row.
+// Sum of (hi, lo) 128-bit unsigned values over the block (fixed tree, exact);
+// every thread receives the total.
+__device__ __forceinline__ void block_sum_u128(unsigned long long &hi, unsigned long long &lo,
+                                               unsigned long long (*sh)[WR_THREADS]) {
+    sh[0][threadIdx.x] = hi;
+    sh[1][threadIdx.x] = lo;
+    __syncthreads();
+    for (int s = WR_THREADS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            const unsigned long long l = sh[1][threadIdx.x] + sh[1][threadIdx.x + s];
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + s] + (l < sh[1][threadIdx.x] ? 1ull : 0ull);
+            sh[1][threadIdx.x] = l;
+        }
+        __syncthreads();
+    }
+    hi = sh[0][0];
+    lo = sh[1][0];
+    __syncthreads();
+}
+
+// Pass 1, one CTA per cluster: size of the new row, ||s_j|| (the squared
+// integer sums added exactly in 128 bits, one rounding to FP64) and
+// <s_j, mu_j^[r-1]> in FP64 over the previous row.
 // Other clusters keep their row (sizes and objective pieces as in k_write_rows).
 __global__ void __launch_bounds__(WR_THREADS) k_acc_rows1(
     int32_t k, const int64_t *flag, const int64_t *cnt, const int64_t *acc_off, const int32_t *clu_doff,
@@ -510,6 +531,7 @@ __global__ void __launch_bounds__(WR_THREADS) k_acc_rows1(
     const double *snorm_old, int64_t *sz, double *snorm_new, double *jA, double *jU) {
     __shared__ double sh[WR_THREADS];
     __shared__ long long shl[WR_THREADS];
+    __shared__ unsigned long long sh128[2][WR_THREADS];
     const int j = blockIdx.x;
     if (j >= k) return;
     const int64_t cb = coff_old[j], ce = coff_old[j + 1];
@@ -525,19 +547,23 @@ __global__ void __launch_bounds__(WR_THREADS) k_acc_rows1(
     }
     const int64_t base = acc_off[j], L = acc_off[j + 1] - base;
     long long nz = 0;
-    double ss = 0.0;
+    // ||S||^2 of the integer sums, exactly, as a 128-bit integer: the FP64 pipe
+    // of this GPU retires about one operation per clock and SM, the integer
+    // pipe dozens. Entries are non-negative (sums of positive member values)
+    // and ||S|| = ||s_j|| 2^shift <= |C_j| 2^shift < 2^63, so the sum of
+    // squares stays below 2^126.
+    unsigned long long ss_hi = 0ull, ss_lo = 0ull;
     // rows start at even entries and have even lengths: 16-byte loads, two
     // of them in flight per thread
-    // FP64 is a slow pipe on this GPU: sum v^2 and v * u on the integers'
-    // doubles and apply the power-of-two scale once at the end (exact, so the
-    // results are the same as scaling every term)
     const longlong2 *row = reinterpret_cast<const longlong2 *>(acc + base);
     const int64_t L2 = L >> 1;
     auto take = [&](long long v) {
         if (v) {
             ++nz;
-            const double x = (double)v;
-            ss += x * x;
+            const unsigned long long u = (unsigned long long)v;
+            const unsigned long long lo = u * u;
+            ss_lo += lo;
+            ss_hi += __umul64hi(u, u) + (ss_lo < lo ? 1ull : 0ull);
         }
     };
     for (int64_t p = threadIdx.x; p < L2; p += 2 * WR_THREADS) {
@@ -549,7 +575,9 @@ __global__ void __launch_bounds__(WR_THREADS) k_acc_rows1(
         take(b.y);
     }
     nz = block_sum_ll(nz, shl);
-    const double nrm = sqrt(block_sum_fixed(ss, sh) * (inv_scale * inv_scale));
+    block_sum_u128(ss_hi, ss_lo, sh128);
+    // the exact sum to FP64 (one rounding of each half), then the power-of-two scale
+    const double nrm = sqrt(((double)ss_hi * 18446744073709551616.0 + (double)ss_lo) * (inv_scale * inv_scale));
     double dot = 0.0;
     const int32_t doff = clu_doff[j];
     for (int64_t q = cb + threadIdx.x; q < ce; q += WR_THREADS)
@@ -592,7 +620,15 @@ __global__ void __launch_bounds__(WR_THREADS) k_acc_rows2(
     const int64_t base = acc_off[j], L2 = (acc_off[j + 1] - base) >> 1;  // entry pairs (even rows)
     const longlong2 *row = reinterpret_cast<const longlong2 *>(acc + base);
     const int32_t doff = clu_doff[j];
-    const double f = inv_scale / snorm_new[j];
+    // u = S * (2^-shift / ||s_j||) in FP32 from the integer sum S (split in
+    // 32-bit halves, each converted with one rounding): at most 4 roundings,
+    // a relative error below 2.4e-7, with no FP64 operation per entry
+    const float ff = (float)(inv_scale / snorm_new[j]);
+    auto value = [&](long long v) {
+        const unsigned long long u = (unsigned long long)v;
+        const float fs = fmaf(__uint2float_rn((unsigned)(u >> 32)), 4294967296.0f, __uint2float_rn((unsigned)u));
+        return fs * ff;
+    };
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int64_t o = o0;
     for (int64_t c0 = 0; c0 < L2; c0 += (int64_t)WR_THREADS * PER) {
@@ -635,7 +671,7 @@ __global__ void __launch_bounds__(WR_THREADS) k_acc_rows2(
                 if (!pv[e]) continue;
                 if (!over) {
                     cterm_new[pos] = (int32_t)(t + e) + doff;
-                    cval_new[pos] = (float)((double)pv[e] * f);
+                    cval_new[pos] = value(pv[e]);
                     cclu_new[pos] = j;
                 }
                 ++pos;

@@ -64,7 +64,8 @@ def test_sampled_oracle_step_on_a_small_corpus():
 
 def test_roofline_bound_follows_the_serving_memory():
     """The roofline names the memory that serves most of the algorithmic
-    bytes: the posting structures count as L2-served only when they fit in L2."""
+    bytes: the posting structures count as L2-served when they fit in L2, and
+    any rate above the HBM peak is L2-served."""
     sys.path.insert(0, ROOT)
     import bench
     from synth import CONFIGS
@@ -78,8 +79,13 @@ def test_roofline_bound_follows_the_serving_memory():
     alg = 57_000_000 * 8 + (w.N + 1) * 8 + w.N * 16 + w.k + 4e10 * 6
     assert r["achieved"] == pytest.approx(alg / 0.010 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 20000.0)
+    # a file larger than L2 at that rate (above the HBM peak): still L2-served
     r = bench.roofline(per, w, 57_000_000, "fp32", peaks, 6800.0, big, 0)
+    assert r["bound"] == "l2"
+    slow = [dict(per[0], ms_assign=100.0)]
+    r = bench.roofline(slow, w, 57_000_000, "fp32", peaks, 6800.0, big, 0)
     assert r["bound"] == "hbm" and r["peak"] == 6800.0
+    assert r["frac"] == pytest.approx(alg / 0.100 / 1e9 / 6800.0)
     # dense rows that fit in L2 serve their bytes from L2 even when the sparse file does not fit
     per = [dict(ms_assign=10.0, ms_update=1.0, postings=3e9, dense_postings=2e9, dense_entries=4e10, simcalc=0)]
     r = bench.roofline(per, w, 57_000_000, "bf16", peaks, 6800.0, big, small)
