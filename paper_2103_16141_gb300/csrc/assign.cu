@@ -123,6 +123,38 @@ __device__ __forceinline__ Top2 top2_merge(Top2 a, Top2 b) {
     return r;
 }
 
+// One thread's running top-2 over score positions: the best score with its
+// position (-1: none) and the second score. A cluster id is looked up only
+// when two scores tie (lowest id wins), and once for the winner at the end,
+// instead of at every new best: those lookups are dependent global loads.
+struct PosTop2 {
+    uint32_t bv;
+    int bp;
+    long long sv;
+};
+
+template <typename IdAt>
+__device__ __forceinline__ void pos_push(PosTop2 &t, uint32_t v, int p, const IdAt &id_at) {
+    if (t.bp < 0 || v > t.bv) {
+        if (t.bp >= 0) t.sv = max(t.sv, (long long)t.bv);
+        t.bv = v;
+        t.bp = p;
+    } else {
+        t.sv = max(t.sv, (long long)v);
+        if (v == t.bv && id_at(p) < id_at(t.bp)) t.bp = p;
+    }
+}
+
+// the same top-2 as top2_push over the same scores, with the winner's id
+template <typename IdAt>
+__device__ __forceinline__ Top2 pos_top2(const PosTop2 &t, const IdAt &id_at) {
+    Top2 r;
+    r.bv = t.bv;
+    r.bi = t.bp >= 0 ? id_at(t.bp) : INT32_MAX;
+    r.sv = t.sv;
+    return r;
+}
+
 __device__ __forceinline__ Top2 top2_shfl(Top2 t, int o) {
     Top2 r;
     r.bv = __shfl_xor_sync(0xffffffffu, t.bv, o);
@@ -784,23 +816,20 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
         // ---- argmax over the candidates (Algorithm 4, lines 14-16) ----
         // largest score, lowest cluster id on ties (ids are looked up only
         // when a score ties or beats the running best)
-        Top2 t;
-        t.bv = 0u;
-        t.bi = INT32_MAX;
-        t.sv = -1;
-        auto push = [&](uint32_t v, int p) {
-            if (t.bi == INT32_MAX || v >= t.bv) top2_push(t, v, id_at(p));
-            else t.sv = max(t.sv, (long long)v);
-        };
+        PosTop2 pt;
+        pt.bv = 0u;
+        pt.bp = -1;
+        pt.sv = -1;
         if (!sub) {
-            for (int p = tid; p < km; p += T) push(rho_ld<GRHO>(rho + p), p);
+            for (int p = tid; p < km; p += T) pos_push(pt, rho_ld<GRHO>(rho + p), p, id_at);
         } else {
             for (int m = tid; m < n_mov; m += T) {
                 const int p = mov_at(m);
-                push(rho_ld<GRHO>(rho + p), p);
+                pos_push(pt, rho_ld<GRHO>(rho + p), p, id_at);
             }
-            if (tid == 0) top2_push(t, own_q, a_loc);
         }
+        Top2 t = pos_top2(pt, id_at);
+        if (sub && tid == 0) top2_push(t, own_q, a_loc);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t = top2_merge(t, top2_shfl(t, o));
         if (lane == 0) warp_t[warp] = t;
@@ -1122,15 +1151,13 @@ __global__ void __launch_bounds__(LIGHT_WARPS * 32, 4) assign_light_kernel(Assig
             __syncwarp();
         }
         // argmax over the moving clusters plus the own cluster (carried score)
-        Top2 t;
-        t.bv = 0u;
-        t.bi = INT32_MAX;
-        t.sv = -1;
-        for (int p = lane; p < n_mov; p += 32) {
-            const uint32_t v = rho[p];
-            if (t.bi == INT32_MAX || v >= t.bv) top2_push(t, v, P.pos_clu[k_off + p]);
-            else t.sv = max(t.sv, (long long)v);
-        }
+        auto id_at = [&](int p) { return P.pos_clu[k_off + p]; };
+        PosTop2 pt;
+        pt.bv = 0u;
+        pt.bp = -1;
+        pt.sv = -1;
+        for (int p = lane; p < n_mov; p += 32) pos_push(pt, rho[p], p, id_at);
+        Top2 t = pos_top2(pt, id_at);
         if (lane == 0) top2_push(t, own_q, a_loc);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t = top2_merge(t, top2_shfl(t, o));
