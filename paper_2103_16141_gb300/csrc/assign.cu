@@ -700,7 +700,8 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
                     int h = first_greater<T>(s_item, it0);
                     int h_first = h ? s_item[h - 1] : 0, h_end = s_item[h];
                     int4 sg = s_seg[h];
-                    for (int it = it0; it < it1; ++it) {
+                    for (int it = it0; it < it1;) {
+                        int step = 1;
                         if (it >= h_end) {
                             do {
                                 ++h;
@@ -712,7 +713,24 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
                         const int sb = sg.x, fb = sg.y, r0 = sg.z;
                         const float vs = __int_as_float(sg.w);
                         const int off = (it - h_first) * CH;
-                        if (off + SC_BLK < r0) {  // two full blocks
+                        if (off + CH + SC_BLK < r0 && it + 1 < it1 && it + 1 < h_end) {
+                            // this item and the next are two full blocks each in
+                            // the same segment: four loads in flight
+                            const int pos = sb + off + 4 * lane;
+                            const Post4 a = load_tiled<PREC, CID16>(P, pos);
+                            const Post4 b = load_tiled<PREC, CID16>(P, pos + SC_BLK);
+                            const Post4 c = load_tiled<PREC, CID16>(P, pos + 2 * SC_BLK);
+                            const Post4 e = load_tiled<PREC, CID16>(P, pos + 3 * SC_BLK);
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) add(a.id[m], vs * a.u[m]);
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) add(b.id[m], vs * b.u[m]);
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) add(c.id[m], vs * c.u[m]);
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) add(e.id[m], vs * e.u[m]);
+                            step = 2;
+                        } else if (off + SC_BLK < r0) {  // two full blocks
                             const int pos = sb + off + 4 * lane;
                             const Post4 a = load_tiled<PREC, CID16>(P, pos);
                             const Post4 b = load_tiled<PREC, CID16>(P, pos + SC_BLK);
@@ -743,6 +761,7 @@ __global__ void __launch_bounds__(T, CB ? 8 : assign_min_blocks<T>()) assign_ker
                                     if (32 * m + lane < rem) add(id[m], vs * u[m]);
                             }
                         }
+                        it += step;
                     }
                 }
             }
