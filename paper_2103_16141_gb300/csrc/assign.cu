@@ -1476,8 +1476,9 @@ cudaError_t autotune_assign(sivf_ctx *c) {
     // the trial steps read a^[r-1] and lambda^[r-1] as the real step will
     SIVF_CUDA_TRY(cudaMemcpyAsync(c->labels_prev, c->labels, sizeof(int32_t) * c->N, cudaMemcpyDeviceToDevice, s));
     SIVF_CUDA_TRY(cudaMemcpyAsync(c->lam_prev, c->lam, c->k, cudaMemcpyDeviceToDevice, s));
-    int dev_smem = 0;
+    int dev_smem = 0, sm_smem = 0;
     SIVF_CUDA_TRY(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    SIVF_CUDA_TRY(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device));
     const int kpad = (c->kmax + 3) & ~3;
     const int def_t = c->assign_threads, def_g = c->assign_global;
     cudaEvent_t e0 = c->ev[0], e1 = c->ev[1];
@@ -1511,7 +1512,13 @@ cudaError_t autotune_assign(sivf_ctx *c) {
     for (int g = 0; g < 2; ++g) {
         if (g == 1 && !c->grho) continue;
         for (int t : threads) {
-            if (!g && (size_t)kpad * 4 + (size_t)t * ASSIGN_STAGE_BYTES > (size_t)dev_smem) continue;
+            const size_t cta_smem = (size_t)kpad * 4 + (size_t)t * ASSIGN_STAGE_BYTES;
+            if (!g && cta_smem > (size_t)dev_smem) continue;
+            // a shared score vector whose size lets fewer than 512 threads
+            // reside per SM is not tried (at k = 20,000 the 32- to 128-thread
+            // CTAs ran 3-16x longer than 512 threads); 512-thread CTAs always
+            // qualify when they fit
+            if (!g && t < 512 && (size_t)sm_smem / (cta_smem + 1024) * (size_t)t < 512) continue;
             float ms = 0.f;
             SIVF_CUDA_TRY(trial(t, g, &ms));
             if (ms < 1e29f) cands.push_back({t, g, ms});
