@@ -75,7 +75,9 @@ typedef struct {
                             round trip); 0: every step launched from the host */
     int autotune;        /* 1: at the second assignment, time every feasible assignment
                             kernel configuration (threads per CTA x score vector in shared
-                            or global memory) on the live state and keep the fastest;
+                            or global memory; a shared score vector that lets fewer than
+                            512 threads reside per SM is not tried) on the live state and
+                            keep the fastest;
                             threads / ctas_per_sm then only seed the search. The choice
                             is remembered for the process (per device and problem
                             shape), so later contexts of the same shape skip the trials */
