@@ -222,7 +222,10 @@ sivf_status sivf_assign(sivf_ctx *ctx, int64_t *n_changed);
 
 /*
  * sivf_update — one update step (Algorithm 5): means of the moving clusters,
- * normalised to unit length in FP64 and stored as FP32; invariant and empty
+ * normalised to unit length and stored as FP32 (norm in FP64: dense form from
+ * the exact 128-bit sum of the squared integer sums, values scaled in FP32
+ * within 2.4e-7 of the exactly rounded quotient; sort form in FP64 throughout);
+ * invariant and empty
  * clusters keep their centroid; the structured inverted file is rebuilt
  * (moving centroids in front, invariant behind, ascending ids in each part).
  * Requires at least one assignment (or sivf_set_labels) since sivf_init.
