@@ -664,6 +664,9 @@ def main():
     trec = recorded_traffic(w, prec)
     roof["traffic"] = trec["dram_bytes_per_launch"] if trec else None
     roof["traffic_launch"] = trec.get("launch") if trec else None
+    # the captured launch's own algorithmic bytes: traffic compares with this,
+    # not with the window's mean bytes_per_launch (the iterations differ)
+    roof["traffic_launch_algorithmic_bytes"] = trec.get("algorithmic_bytes_per_launch") if trec else None
 
     # the FP32 path on the same window
     vs_fp32 = None
