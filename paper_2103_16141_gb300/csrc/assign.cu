@@ -1,19 +1,26 @@
 // Assignment step of SIVF (Algorithm 4, Section 4.1; Algorithm 2 when the
-// ICP filter is off) on sm_103a.
+// ICP filter is off; Algorithm 3, IVF-CBICP, as an ablation) on sm_103a.
 //
 // One CTA scores one object at a time (persistent CTAs pull object ids from a
-// global counter). The k similarities rho_j live in shared memory as unsigned
-// fixed-point sums with quantum 2^-31: each posting adds
-// q = ceil(fl(v * u) * 2^31) with an integer shared-memory atomic. Integer
-// addition is associative, so the sums do not depend on the order in which
-// threads visit postings: the filtered and unfiltered modes produce identical
-// scores, and every run is deterministic.
+// global counter); filtered objects of instances with few moving clusters
+// take a warp each instead (assign_light_kernel). The k similarities rho_j
+// live in shared memory as unsigned fixed-point sums with quantum 2^-31,
+// indexed by scan position (the moving clusters first):
+//  - a term held as a sparse posting list adds q = ceil(fl(v * u) * 2^31) per
+//    posting with an integer shared-memory atomic;
+//  - a term with a dense row (the lists that hold a large share of the
+//    clusters) is read with 16-byte loads; for every chunk of staged terms the
+//    dense terms' products are chained in FP32 fused multiply-adds per score
+//    position, and the chain's ceil is added once.
+// Integer addition is associative, so the sums do not depend on the order in
+// which threads visit postings: the filtered and unfiltered modes produce
+// identical scores, and every run is deterministic.
 //
 // ICP gate (Algorithm 4, line 6): if lambda^[r-1] of the object's cluster is 1,
-// only the front part [off_s, off_s + mf0_s) of each posting list is scanned,
-// and the candidates are the moving centroids plus the object's own cluster,
-// whose score is carried from its previous scan (it is unchanged because that
-// centroid is invariant).
+// only the front of each posting list (the moving prefix of a dense row) is
+// scanned, and the candidates are the moving centroids plus the object's own
+// cluster, whose score is carried from its previous scan (it is unchanged
+// because that centroid is invariant).
 //
 // Argmax (Algorithm 4, lines 14-16): largest score, lowest index on ties.
 // Every object whose top-2 margin lies inside the rigorous error bound E of
@@ -23,12 +30,16 @@
 // whatever the posting precision.
 //
 // Error bound (all terms v > 0, u > 0; master value u, stored value u~ with
-// |u~ - u| <= eps*u + eta; n terms in the object, S = sum of its values):
-//   |rho~ - rho| <= c*rho + a,  c = 2^-24 (1 + eps) + eps,
-//                               a = n * 2^-31 + (1 + 2^-24) * eta * S
+// |u~ - u| <= eps*u + eta; n terms in the object, nd of them dense,
+// S = sum of its values):
+//   |rho~ - rho| <= c*rho + a,  g = m 2^-24 / (1 - m 2^-24), m = max(1, nd),
+//                               c = eps + (1 + eps) * g,
+//                               a = 2n * 2^-31 + (1 + g) * eta * S
 //   =>  E(rho~) = (c * rho~ + a) / (1 - c).
-// The 2^-24 term is the FP32 rounding of the product, n * 2^-31 the one-sided
-// fixed-point rounding of the n products.
+// g covers the FP32 rounding of a sparse product or a chain of up to nd fused
+// multiply-adds; 2n quanta cover the one-sided ceilings (one per sparse
+// posting, one per dense chain). eps = 0, 2^-8, 2^-11 and eta = 0, 0, 2^-38
+// for FP32, BF16, FP16 postings.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
