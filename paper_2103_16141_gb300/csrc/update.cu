@@ -1,23 +1,33 @@
 // Update step of SIVF (Algorithm 5, Section 4.2) on sm_103a, plus the
 // set-up kernels (CSR validation, seed centroids).
 //
-// Pipeline for iteration r (lambda = lambda^[r] from the assignment):
-//  u1  stable radix sort of (label, object id): members of each cluster in
-//      ascending object id; per-cluster member counts.
-//  u2  for every moving, non-empty cluster ("recomputed"), expand its members'
-//      (term, value) pairs in member order, stable-sort them by
-//      (cluster rank, term) and reduce equal keys sequentially in FP64. The sum
-//      of each (cluster, term) therefore accumulates in ascending object id,
-//      the order of the plain definition (Algorithm 5, lines 17-20), and is
-//      reproducible bit for bit.
-//  u3  ||s_j|| in FP64 (fixed reduction tree), u = s / ||s|| stored as FP32
-//      (dividing by |C_j| first cancels exactly and is skipped); the objective
-//      pieces sum_j <s_j, mu_j^[r-1]> and sum_j ||s_j||.
+// Pipeline for iteration r (lambda = lambda^[r] from the assignment), in the
+// default dense form:
+//  u1  per-cluster member counts from the labels.
+//  u2  an int64 fixed-point accumulator row of the instance's D terms per
+//      cluster, kept across iterations: every object whose label changed
+//      moves its q(x) = ceil(x 2^shift) values from its old cluster's row to
+//      the new one with integer atomics (k_acc_scatter). Integer sums are
+//      exact, so each entry is the sum over the current members whatever the
+//      history, and the result is deterministic.
+//  u3  pass 1 (k_acc_rows1): new row sizes, ||s_j|| from the exact 128-bit
+//      sum of the squared integer sums (one rounding to FP64), and the
+//      objective pieces <s_j, mu_j^[r-1]>; pass 2 (k_acc_rows2): the row
+//      compacted in ascending term order, u = S (2^-shift / ||s_j||) in FP32.
+//      Dividing by |C_j| first cancels exactly and is skipped.
 //  u4  invariant and empty clusters keep their centroid row (copied).
-//  u5  structured inverted file: stable radix sort of the centroid entries by
-//      (term, lambda_j); the cluster-major input is in ascending j, so each
-//      term's list holds the moving centroids first and the invariant ones
-//      after, ascending ids in each part (Algorithm 5, lines 1-14 and 21-30).
+//  u5  the scan structures of the structured inverted file, counted per term
+//      and part (k_if_count) and written in one scatter pass over the
+//      centroid entries (k_scan_fill): the scan order (moving
+//      clusters first), the dense head rows and the sparse scan copy, whose
+//      lists hold the moving centroids first and the invariant ones after
+//      (Algorithm 5, lines 1-14 and 21-30). The canonical sorted file (ids
+//      ascending in each part) is built by a stable radix sort only when a
+//      getter asks for it.
+// The sort form replaces u1-u3 by a stable radix sort of (label, object id),
+// an expansion of the recomputed clusters' members' (term, value) pairs sorted
+// by (cluster rank, term) and reduced sequentially in FP64, in ascending
+// object id, the order of the plain definition (Algorithm 5, lines 17-20).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
