@@ -43,6 +43,12 @@
 //                                        of 8 entries; a term's list becomes a row when it
 //                                        holds at least dense_frac of its instance's k
 //                                        (raised while the rows would exceed cap_dense).
+//   update accumulator    acc int64 (dense form): one row of the instance's D terms per
+//                                        cluster (acc_off), the fixed-point sums
+//                                        q(x) = ceil(x 2^shift) of the current members,
+//                                        kept across iterations
+//   object lists          heavy_ids, light_ids int32[N]: the objects of the CTA and the
+//                                        warp-per-object assignment kernels
 #pragma once
 
 #include <cuda_runtime.h>
